@@ -1,0 +1,282 @@
+"""Checks that tie the FP64 oracle to facts fixed by the paper and by mathematics, not to itself.
+
+Each ``pin_*`` function takes an ``oracle.Oracle`` factory and returns a (passed, detail) pair, so
+that the same checks serve the pin tests (which assert them) and the mutation test (which plants
+a mistake in a copy of the oracle and expects at least one pin to fail).
+"""
+import numpy as np
+
+import hisq_inputs as hi
+import oracle.dense as dense
+
+
+def _rand_vec(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _fields(dims, seed_shift=0):
+    lat = hi.Lattice(dims)
+    return lat, hi.fat_links(lat, seed_u=1 + seed_shift, seed_noise=2 + seed_shift), \
+        hi.naik_links(lat, seed_u=3 + seed_shift)
+
+
+def pin_matrix_form(make, dims=(4, 4, 4, 4), tol=1e-13):
+    """Stencil oracle equals the sparse matrix assembled block by block from Eq. (3), on the full
+    lattice and for both even-odd blocks."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(11)
+    D = dense.dslash_matrix(dims, X, N)
+    v = _rand_vec(rng, (2, lat.volume, 3))
+    worst = 0.0
+    w = o.dslash_full(v)
+    for k in range(2):
+        worst = max(worst, _rel(w[k].ravel(), D @ v[k].ravel()))
+    deo, doe = dense.even_odd_blocks(dims, X, N)
+    ve = _rand_vec(rng, (lat.half_volume, 3))
+    worst = max(worst, _rel(o.dslash_eo(ve, 1).ravel(), doe @ ve.ravel()))
+    worst = max(worst, _rel(o.dslash_eo(ve, 0).ravel(), deo @ ve.ravel()))
+    return worst <= tol, f"max rel diff {worst:.3e} on {dims}"
+
+
+def pin_anti_hermitian(make, dims=(8, 4, 6, 4), tol=1e-14):
+    """<u, D_eo v> = -<D_oe u, v> and <u, D v> = -<D u, v> (D is anti-Hermitian for any links)."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(12)
+    u = _rand_vec(rng, (lat.half_volume, 3))
+    v = _rand_vec(rng, (lat.half_volume, 3))
+    lhs = np.vdot(u, o.dslash_eo(v, 0))
+    rhs = -np.vdot(o.dslash_eo(u, 1), v)
+    err1 = abs(lhs - rhs) / abs(lhs)
+    uf = _rand_vec(rng, (lat.volume, 3))
+    vf = _rand_vec(rng, (lat.volume, 3))
+    a = np.vdot(uf, o.dslash_full(vf))
+    b = -np.vdot(o.dslash_full(uf), vf)
+    err2 = abs(a - b) / abs(a)
+    return max(err1, err2) <= tol, f"eo {err1:.2e} full {err2:.2e}"
+
+
+def gauge_transform(lat, X, N, omega):
+    """X'_{x,mu} = W_x X_{x,mu} W^dag_{x+mu}, N'_{x,mu} = W_x N_{x,mu} W^dag_{x+3mu}."""
+    c = lat.coords()
+    Xp = np.empty_like(X)
+    Np = np.empty_like(N)
+    for mu in range(4):
+        for step, src, dst in ((1, X, Xp), (3, N, Np)):
+            cc = c.copy()
+            cc[:, mu] = (cc[:, mu] + step) % lat.dims[mu]
+            lx, ly, lz, _ = lat.dims
+            nb = cc[:, 0] + lx * (cc[:, 1] + ly * (cc[:, 2] + lz * cc[:, 3]))
+            dst[mu] = omega @ src[mu] @ omega[nb].conj().swapaxes(-1, -2)
+    return Xp, Np
+
+
+def pin_gauge_covariance(make, dims=(8, 4, 4, 6), tol=1e-13):
+    """D' (W v) = W (D v) for a random SU(3) gauge transform W, full lattice and even-odd."""
+    lat, X, N = _fields(dims)
+    om = hi.gauge_transform_field(lat)
+    Xp, Np = gauge_transform(lat, X, N, om)
+    o, op = make(dims, X, N), make(dims, Xp, Np)
+    rng = np.random.default_rng(13)
+    v = _rand_vec(rng, (lat.volume, 3))
+    lhs = op.dslash_full(np.einsum("xab,xb->xa", om, v))
+    rhs = np.einsum("xab,xb->xa", om, o.dslash_full(v))
+    err = _rel(lhs, rhs)
+    ve = _rand_vec(rng, (lat.half_volume, 3))
+    ev, od = lat.eo_sites(0), lat.eo_sites(1)
+    lhs = op.dslash_eo(np.einsum("xab,xb->xa", om[ev], ve), 1)
+    rhs = np.einsum("xab,xb->xa", om[od], o.dslash_eo(ve, 1))
+    err = max(err, _rel(lhs, rhs))
+    return err <= tol, f"rel {err:.2e}"
+
+
+def free_field_eigenvalue(dims, k, mass, c1, c3, antiperiodic_t=True):
+    """Closed form: A = m^2 - D_eo D_oe on the plane wave exp(i p.x) restricted to even sites has
+    eigenvalue m^2 + 4 sum_mu (c1 sin p_mu + c3 sin 3 p_mu)^2, p_mu = 2 pi k_mu / L_mu
+    (k_t + 1/2 for the antiperiodic t direction).  Follows from D^2 = sum_mu S_mu^2 for unit
+    links, because the staggered phases anticommute between directions."""
+    p = [2 * np.pi * (k[mu] + (0.5 if (mu == 3 and antiperiodic_t) else 0.0)) / dims[mu] for mu in range(4)]
+    return mass ** 2 + 4 * sum((c1 * np.sin(q) + c3 * np.sin(3 * q)) ** 2 for q in p), p
+
+
+def plane_wave_even(lat, p, colour):
+    c = lat.coords()[lat.eo_sites(0)]
+    f = np.zeros((lat.half_volume, 3), dtype=np.complex128)
+    f[:, colour] = np.exp(1j * (c @ np.asarray(p)))
+    return f
+
+
+def pin_free_field_plane_waves(make, dims=(8, 8, 6, 10), mass=0.3, tol=1e-13, n_modes=12):
+    """A applied to even-site plane waves of the unit-link field returns the closed-form
+    eigenvalue times the wave (checks directions, hop lengths 1 and 3, signs, coefficients and
+    the antiperiodic boundary)."""
+    lat = hi.Lattice(dims)
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    X, N = hi.free_field_links(lat, c1, c3)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(14)
+    worst = 0.0
+    for _ in range(n_modes):
+        k = [int(rng.integers(0, d)) for d in dims]
+        lam, p = free_field_eigenvalue(dims, k, mass, c1, c3)
+        f = plane_wave_even(lat, p, int(rng.integers(0, 3)))
+        worst = max(worst, _rel(o.aop(f, mass), lam * f))
+    return worst <= tol, f"max rel {worst:.2e}"
+
+
+def pin_free_field_spectrum(make, dims=(4, 4, 4, 6), mass=0.2, tol=1e-11):
+    """Sorted eigenvalues of the matrix of A (built column by column from the oracle) equal the
+    closed-form free-field spectrum with multiplicities."""
+    lat = hi.Lattice(dims)
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    X, N = hi.free_field_links(lat, c1, c3)
+    o = make(dims, X, N)
+    n = lat.half_volume * 3
+    eye = np.eye(n, dtype=np.complex128).reshape(n, lat.half_volume, 3)
+    A = o.aop(eye, mass).reshape(n, n).T
+    got = np.sort(np.linalg.eigvalsh(0.5 * (A + A.conj().T)))
+    vals = []
+    for kx in range(dims[0]):
+        for ky in range(dims[1]):
+            for kz in range(dims[2]):
+                for kt in range(dims[3]):
+                    vals += [free_field_eigenvalue(dims, (kx, ky, kz, kt), mass, c1, c3)[0]] * 3
+    want = np.sort(vals)[::2]  # p and p + (pi,pi,pi,pi) coincide on even sites
+    herm = _rel(A, A.conj().T)
+    err = float(np.max(np.abs(got - want)) / np.max(want))
+    return err <= tol and herm <= 1e-14, f"spectrum {err:.2e}, hermiticity {herm:.2e}"
+
+
+def pin_cg_dense_solve(make, dims=(4, 4, 4, 6), mass=0.1, tol=1e-10):
+    """Oracle CG meets the true residual and agrees with a dense direct solve of the matrix A
+    assembled from Eq. (3)."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    b = hi.gaussian_rhs(lat, 0)
+    x, it, rel = o.cg(b, mass, tol=tol)
+    A = dense.a_matrix(dims, X, N, mass).toarray()
+    xd = np.linalg.solve(A, b.ravel())
+    ev = np.linalg.eigvalsh(A)
+    kappa = ev[-1] / ev[0]
+    err = _rel(x.ravel(), xd)
+    true = np.linalg.norm(b.ravel() - A @ x.ravel()) / np.linalg.norm(b)
+    ok = it > 0 and rel <= tol and true <= tol * 1.01 and err <= kappa * tol and it <= A.shape[0]
+    return ok, f"iters {it}, true {true:.2e}, |x-xd|/|xd| {err:.2e}, kappa {kappa:.1f}"
+
+
+def pin_cg_free_field_exact(make, dims=(8, 8, 8, 8), mass=0.05, tol=1e-10):
+    """CG on the unit-link field reproduces the momentum-space solution x = sum c_p f_p / lambda_p
+    for a right-hand side made of a few plane waves."""
+    lat = hi.Lattice(dims)
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    X, N = hi.free_field_links(lat, c1, c3)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(15)
+    b = np.zeros((lat.half_volume, 3), dtype=np.complex128)
+    x_exact = np.zeros_like(b)
+    for _ in range(5):
+        k = [int(rng.integers(0, d)) for d in dims]
+        lam, p = free_field_eigenvalue(dims, k, mass, c1, c3)
+        coef = complex(rng.standard_normal(), rng.standard_normal())
+        f = plane_wave_even(lat, p, int(rng.integers(0, 3)))
+        b += coef * f
+        x_exact += coef * f / lam
+    x, it, rel = o.cg(b, mass, tol=tol)
+    err = _rel(x, x_exact)
+    return it > 0 and err <= 1e-8, f"iters {it}, rel err {err:.2e}"
+
+
+def network_weights_identity():
+    """Weights with only the identity path of channel 0 set: the network is the identity."""
+    W1 = np.zeros((17, 4, 1), complex); W1[0, 0, 0] = 1
+    W2 = np.zeros((17, 4, 4), complex); W2[0, 0, 0] = 1
+    W3 = np.zeros((17, 1, 4), complex); W3[0, 0, 0] = 1
+    return np.concatenate([W1.ravel(), W2.ravel(), W3.ravel()])
+
+
+def network_weights_aop(mass):
+    """Weights for which the network computes A r = m^2 r - D_eo D_oe r: channel 0 carries
+    D(D r) through the hop paths (+1 on forward, -1 on backward hops reproduces Eq. (3)),
+    channel 1 carries r through the identity path."""
+    hop = np.zeros(17, complex)
+    for mu in range(4):
+        hop[1 + 2 * mu], hop[2 + 2 * mu] = 1, -1
+        hop[9 + 2 * mu], hop[10 + 2 * mu] = 1, -1
+    W1 = np.zeros((17, 4, 1), complex); W1[:, 0, 0] = hop; W1[0, 1, 0] = 1
+    W2 = np.zeros((17, 4, 4), complex); W2[:, 0, 0] = hop; W2[0, 1, 1] = 1
+    W3 = np.zeros((17, 1, 4), complex); W3[0, 0, 0] = -1; W3[0, 0, 1] = mass ** 2
+    return np.concatenate([W1.ravel(), W2.ravel(), W3.ravel()])
+
+
+def pin_network_special_weights(make, dims=(8, 4, 4, 6), mass=0.2, tol=1e-13):
+    """Identity weights give the identity; the weights that spell out Eq. (3) twice give A."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    r = hi.gaussian_rhs(lat, 3)
+    e1 = _rel(o.pc_forward(network_weights_identity(), r), r)
+    e2 = _rel(o.pc_forward(network_weights_aop(mass), r), o.aop(r, mass))
+    return max(e1, e2) <= tol, f"identity {e1:.1e}, A {e2:.1e}"
+
+
+def pin_network_covariance(make, dims=(6, 4, 4, 8), tol=1e-13):
+    """The network commutes with gauge transforms: M'(W r) = W (M r)."""
+    lat, X, N = _fields(dims)
+    om = hi.gauge_transform_field(lat)
+    Xp, Np = gauge_transform(lat, X, N, om)
+    o, op = make(dims, X, N), make(dims, Xp, Np)
+    rng = np.random.default_rng(16)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    r = hi.gaussian_rhs(lat, 4)
+    ev = lat.eo_sites(0)
+    lhs = op.pc_forward(W, np.einsum("xab,xb->xa", om[ev], r))
+    rhs = np.einsum("xab,xb->xa", om[ev], o.pc_forward(W, r))
+    err = _rel(lhs, rhs)
+    return err <= tol, f"rel {err:.2e}"
+
+
+def pin_network_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=24, tol=1e-6):
+    """Analytic loss gradient equals central finite differences in Re W and Im W."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(17)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    r = np.stack([hi.gaussian_rhs(lat, 10 + k) for k in range(2)])
+    e = np.stack([hi.gaussian_rhs(lat, 20 + k) for k in range(2)])
+    _, g = o.pc_loss_grad(W, r, e)
+    h = 1e-5
+    worst = 0.0
+    for i in rng.choice(W.size, n_checks, replace=False):
+        for unit, comp in ((1.0, g[i].real), (1j, g[i].imag)):
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i] += unit * h
+            Wm[i] -= unit * h
+            fd = (o.pc_loss_grad(Wp, r, e, False)[0] - o.pc_loss_grad(Wm, r, e, False)[0]) / (2 * h)
+            worst = max(worst, abs(fd - comp) / max(abs(comp), 1e-3 * np.abs(g).max()))
+    return worst <= tol, f"worst rel {worst:.2e}"
+
+
+def pin_fcg_identity_is_cg(make, dims=(4, 4, 4, 6), mass=0.1, tol=1e-10):
+    """Flexible CG with the identity network takes the same iterations as CG and reaches the
+    dense-solve solution."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    b = hi.gaussian_rhs(lat, 5)
+    x1, it1, _ = o.cg(b, mass, tol=tol)
+    x2, it2, rel2 = o.fcg(network_weights_identity(), b, mass, tol=tol)
+    A = dense.a_matrix(dims, X, N, mass).toarray()
+    xd = np.linalg.solve(A, b.ravel())
+    err = _rel(x2.ravel(), xd)
+    return abs(it1 - it2) <= 1 and rel2 <= tol and err <= 1e-7, f"cg {it1} fcg {it2} err {err:.1e}"
+
+
+ALL_PINS = [
+    pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
+    pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
+    pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd,
+    pin_fcg_identity_is_cg,
+]
