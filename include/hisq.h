@@ -1,0 +1,231 @@
+/*
+ * hisq.h - C ABI of the GB300 (sm_103a) multi-right-hand-side even-odd HISQ Dslash and the
+ * conjugate-gradient solvers built on it.
+ *
+ * Operator (Eq. (3), HISQ Dslash in terms of fat links X and Naik links N):
+ *   w_x = sum_{mu=0..3} [ X_{x,mu} v_{x+mu} - X^dag_{x-mu,mu} v_{x-mu}
+ *                        + N_{x,mu} v_{x+3mu} - N^dag_{x-3mu,mu} v_{x-3mu} ]
+ * applied to bundles of n right-hand sides that share one read of the links (Eq. (4)).
+ * Hops of 1 and 3 flip the site parity, so D = [[0, D_eo], [D_oe, 0]]; the solvers work on the
+ * even sites with the Hermitian positive definite A = m^2 - D_eo D_oe.
+ *
+ * Geometry and canonical (exchange) layouts:
+ *   lattice (Lx, Ly, Lz, Lt), every extent even and >= 4; V = Lx Ly Lz Lt.
+ *   lexicographic site index i = x + Lx (y + Ly (z + Lz t)); parity (x+y+z+t) mod 2;
+ *   even-odd index of a site within its parity = i / 2.
+ *   canonical links:   double [4 mu][V][3 row][3 col][2 re/im]
+ *   canonical vectors: double [nrhs][V/2][3 colour][2 re/im], sites of one parity in
+ *                      even-odd order.
+ * Staggered phases and boundary signs are part of the links; the library applies Eq. (3) to
+ * whatever X and N it is given, with periodic index arithmetic.
+ *
+ * Internal vector layout (what hisq_dslash, hisq_aop and the preconditioner read and write):
+ *   site-major, colour, right-hand side innermost: element (s, c, r) at index (s*3 + c)*n + r,
+ *   one complex number per element, stored as
+ *     HISQ_FP64: double2      HISQ_FP32: float2      HISQ_BF16: __nv_bfloat162 (unscaled)
+ *     HISQ_FP16: __half2, followed (after the V/2*3*n half2 array, at a 16-byte aligned
+ *                offset) by one float scale per (site, rhs), index s*n + r; the value of an
+ *                element is half2 * scale.
+ *   hisq_vector_bytes() gives the size of one such bundle.
+ *
+ * Threads and contexts: hisq_init() creates a context bound to the calling host thread (one
+ * lattice, one device, one stream).  Every other call uses the calling thread's context.
+ *
+ * Pointers: arguments named "device" must be device memory of the context's device; arguments
+ * named "host or device" may be either (the library detects which).  Ownership of every buffer
+ * passed in stays with the caller.  Handles (hisq_links, hisq_pc) and the solver workspace are
+ * owned by the library and freed by the matching *_destroy call or by hisq_finalize().
+ *
+ * Errors: every function returns HISQ_OK (0) or a negative hisq_status.  Nothing aborts, traps or
+ * waits without bound.  hisq_last_error() gives a one-line description of the last failure in
+ * the calling thread.
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HISQ_OK = 0,
+    HISQ_ERR_ARG = -1,            /* invalid argument (null pointer, size, precision, parity) */
+    HISQ_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    HISQ_ERR_NOMEM = -3,          /* device or host allocation failed */
+    HISQ_ERR_NOT_CONVERGED = -4,  /* a solve missed its tolerance within max_iter */
+    HISQ_ERR_BREAKDOWN = -5,      /* NaN/Inf or a non-positive <p, A p> in a solve */
+    HISQ_ERR_TIMEOUT = -6,        /* a bounded device-side wait ran out */
+    HISQ_ERR_STATE = -7           /* no context on this thread, or handles of another context */
+} hisq_status;
+
+typedef enum { HISQ_FP64 = 0, HISQ_FP32 = 1, HISQ_FP16 = 2, HISQ_BF16 = 3 } hisq_prec;
+
+#define HISQ_MAX_BUNDLE 16   /* right-hand sides per solver bundle */
+#define HISQ_MAX_NRHS 64     /* right-hand sides per hisq_dslash / hisq_aop call */
+#define HISQ_PC_WEIGHTS 408  /* complex weights of the preconditioner network */
+
+typedef struct hisq_links hisq_links;
+typedef struct hisq_pc hisq_pc;
+
+/* ---- context ------------------------------------------------------------------------------ */
+
+/* Create the calling thread's context: lattice dims[4] = (Lx, Ly, Lz, Lt) (even, >= 4), CUDA
+ * device ordinal, and the cudaStream_t all work is issued on (NULL = the legacy default
+ * stream).  Fails with HISQ_ERR_STATE if the thread already has a context. */
+int hisq_init(const int dims[4], int device, void *cuda_stream);
+
+/* Destroy the calling thread's context and everything it owns (links, preconditioners,
+ * workspace, captured graphs). */
+int hisq_finalize(void);
+
+const char *hisq_strerror(int status);
+const char *hisq_last_error(void);
+
+/* ---- links (row a1 of the hot path: pack once per gauge field) ------------------------------ */
+
+/* Pack one kind of link field for the Dslash.  canon: host or device, canonical layout
+ * double[4][V][3][3][2], the fat links X (is_naik = 0, hop 1) or the Naik links N (is_naik = 1,
+ * hop 3).  prec: storage precision of the copy the Dslash reads.  recon: 18 (full matrix),
+ * or, for Naik links only, 13 (two rows of W plus c, where N = c W, W in SU(3)) or 9 (eight
+ * SU(3) parameters plus c); 13 and 9 are exact only for links of that form (Sec. 2: Naik links
+ * can be rebuilt from 9 or 13/14 reals; fat links cannot).  16-bit 18-real links carry one
+ * float scale per site.  When prec != HISQ_FP64 the handle also keeps an FP64 copy, used by the
+ * solvers' FP64 residual recomputation.  The input is not retained. */
+int hisq_links_create(hisq_links **h, const double *canon, int is_naik, int prec, int recon);
+int hisq_links_destroy(hisq_links *h);
+
+/* Decode the packed copy back to FP64 (the links as the Dslash sees them) for checking:
+ * out (host) double[2 parity][V/2][8 slot][3][3][2], slot 2mu = U_{x,mu} and slot 2mu+1 =
+ * -U^dag_{x-k mu,mu} (k = 1 fat, 3 Naik) for the site x of the given parity and even-odd index. */
+int hisq_links_export(const hisq_links *h, double *out);
+
+/* ---- vectors ------------------------------------------------------------------------------ */
+
+/* Bytes of one internal even-odd bundle of nrhs vectors in precision prec. */
+size_t hisq_vector_bytes(int prec, int nrhs);
+
+/* canonical (host or device, double[nrhs][V/2][3][2]) <-> internal (device) layout. */
+int hisq_pack(const double *canon, void *internal, int nrhs, int prec);
+int hisq_unpack(const void *internal, double *canon, int nrhs, int prec);
+
+/* ---- operators (rows a2, a3) -------------------------------------------------------------- */
+
+/* w = D_{p,1-p} v for nrhs (1..HISQ_MAX_NRHS) right-hand sides, Eq. (3)-(4): the input lives on
+ * parity 1-parity and the output on `parity` (0: D_eo, odd -> even; 1: D_oe, even -> odd).
+ * in, out: device, internal layout in the links' precision; they must not overlap.  fat and
+ * naik must share the context and the precision.  Allocates nothing. */
+int hisq_dslash(const hisq_links *fat, const hisq_links *naik, const void *in, void *out,
+                int nrhs, int parity);
+
+/* A-operator with fused dot product: out = m^2 in - D_eo (D_oe in) on the even sites, and
+ * pAp[r] = Re <in_r, out_r> accumulated in FP64.  in, out: device, internal layout in the links'
+ * precision; pAp: host or device, nrhs doubles (may be NULL).  The odd-parity intermediate lives
+ * in the context's workspace, which grows on demand (cudaMalloc). */
+int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
+             void *out, int nrhs, double *pAp);
+
+/* ---- solvers (rows a4-a6, a9) ------------------------------------------------------------- */
+
+typedef struct {
+    int inner_prec;       /* HISQ_FP64: plain FP64 CG; FP32/FP16/BF16: mixed precision with FP64
+                             reliable updates (needs links packed in that precision) */
+    double delta;         /* reliable update when |r| < delta * |r at the last update| (0.1) */
+    int max_iter;         /* per right-hand side (default 20000) */
+    int bundle;           /* right-hand sides per bundle, 1..HISQ_MAX_BUNDLE; 0 = autotuned */
+    int use_graph;        /* 1: whole solve as one captured CUDA graph with device-side
+                             control flow; 0: host-driven iterations */
+    int check_every;      /* host-driven mode: iterations between residual read-backs (1) */
+    const hisq_pc *pc;    /* learned preconditioner for flexible CG; NULL = plain CG */
+    int stall_window;     /* flexible CG: fall back to plain CG if the residual does not drop */
+    double stall_factor;  /* by stall_factor within stall_window iterations (10, 50) */
+    int autotune;         /* 1: time the Dslash launch shapes on first use of a shape */
+    int time_kernels;     /* 1: record CUDA events around every Dslash launch (stats) */
+} hisq_solver_params;
+
+void hisq_default_solver_params(hisq_solver_params *p);
+int hisq_set_solver_params(const hisq_solver_params *p);
+int hisq_get_solver_params(hisq_solver_params *p);
+
+/* Solve A x_k = rhs_k (A = mass^2 - D_eo D_oe, even sites) for k < nrhs to the relative true
+ * residual |b - A x| / |b| <= tol, checked in FP64 on the GPU.  rhs[k], x[k]: host or device,
+ * canonical double[V/2][3][2] each; x is output only (initial guess 0).  The right-hand sides
+ * are solved in bundles that share every link read; converged ones are masked out.
+ * Returns HISQ_ERR_NOT_CONVERGED (stats filled, x holds the last iterate) if any right-hand
+ * side misses tol within max_iter. */
+int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *const rhs[],
+                  double *x[], int nrhs, double mass, double tol);
+
+typedef struct {
+    int nrhs;
+    int converged;            /* right-hand sides that met tol */
+    int bundles;              /* bundles solved */
+    int bundle_size;          /* right-hand sides per bundle used */
+    int max_iterations;       /* largest per-right-hand-side iteration count */
+    long total_iterations;    /* sum over right-hand sides */
+    long bundle_iterations;   /* sum over bundles of the iterations each bundle ran */
+    int reliable_updates;     /* FP64 residual recomputations, summed over right-hand sides */
+    int fallbacks;            /* flexible-CG stalls that switched to plain CG */
+    double seconds;           /* wall time of the hisq_cg_solve call */
+    double dslash_ms;         /* summed Dslash kernel time (time_kernels = 1 only) */
+    int dslash_launches;      /* Dslash launches timed */
+    double flops;             /* useful flops: (2*1146 + 72) per even site, RHS and iteration */
+} hisq_solve_stats;
+
+/* Statistics of the calling thread's last hisq_cg_solve.  iterations (int[nrhs]) and
+ * true_residual (double[nrhs], FP64 |b - A x| / |b| per right-hand side) are host arrays or
+ * NULL. */
+int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual);
+
+/* Pick and cache the fastest Dslash launch shape for nrhs right-hand sides in the links'
+ * precision (row a6), timing every candidate with CUDA events.  Writes the chosen
+ * right-hand sides per thread and threads per block if the pointers are not NULL. */
+int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int nrhs, int *rhs_per_thread,
+                  int *block_threads);
+
+/* Pin the Dslash launch shape used for nrhs right-hand sides with links of (prec, recon):
+ * rhs_per_thread in {1, 2, 4, 8} dividing nrhs (FP64: 1, 2, 4), block_threads in 32..256.
+ * Overrides the autotuner's choice for that key. */
+int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_thread, int block_threads);
+
+/* ---- learned preconditioner (rows a7-a9) --------------------------------------------------- */
+
+/* A gauge-covariant parallel-transport network, channels 1 -> 4 -> 4 -> 1, 17 paths per layer
+ * (identity, T^{+-1}_mu through X, T^{+-3}_mu through N), complex weights stored as
+ * double[HISQ_PC_WEIGHTS][2]: layer 1 [17][4][1], layer 2 [17][4][4], layer 3 [17][1][4]
+ * ([path][out channel][in channel]); path 0 identity, 1+2mu / 2+2mu the +/- one-hop through X,
+ * 9+2mu / 10+2mu the +/- three-hop through N.  Acts on FP32 internal vectors of the even sites
+ * (zero on odd sites); the output is the even-site part. */
+int hisq_pc_create(hisq_pc **pc, const double *weights /* host, NULL = identity network */);
+int hisq_pc_destroy(hisq_pc *pc);
+int hisq_pc_set_weights(hisq_pc *pc, const double *weights /* host */);
+int hisq_pc_get_weights(const hisq_pc *pc, double *weights /* host */);
+
+/* out = M(in) for nrhs (1..HISQ_MAX_BUNDLE) FP32 internal even-site vectors (device). */
+int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                  const void *in, void *out, int nrhs);
+
+/* Training loss (1/K) sum_k |M r_k - e_k|^2 / |e_k|^2 over K pairs and its gradient
+ * dL/dRe W + i dL/dIm W (host double[HISQ_PC_WEIGHTS][2]); r, e: device FP32 internal bundles
+ * of K (1..HISQ_MAX_BUNDLE) vectors each. */
+int hisq_pc_loss_grad(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                      const void *r, const void *e, int K, double *loss, double *grad);
+
+/* One Adam step (Kingma & Ba) on the real and imaginary parts of the weights, on the GPU:
+ * grad host or device double[HISQ_PC_WEIGHTS][2]; step counts from 1. */
+int hisq_pc_adam_step(hisq_pc *pc, const double *grad, int step, double lr, double beta1,
+                      double beta2, double eps);
+
+/* Train on K pairs (device FP32 internal, stored as ceil(K/16) consecutive bundles of 16
+ * vectors, the last one padded) for `epochs` passes of minibatches of `batch` (<= 16) pairs
+ * with Adam at learning rate lr.  loss_history (host, epochs doubles, may be NULL) receives
+ * the mean loss of each epoch. */
+int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *r,
+                  const void *e, int K, int batch, int epochs, double lr, double *loss_history);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HISQ_H */

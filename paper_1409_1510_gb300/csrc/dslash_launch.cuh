@@ -1,0 +1,58 @@
+// Dispatch from run-time (Naik recon, right-hand sides per thread, epilogue) to the compiled
+// Dslash instantiations of one storage precision.  Each precision lives in its own
+// translation unit so the instantiations compile in parallel.
+#pragma once
+#include "dslash_kernel.cuh"
+
+namespace hisq {
+
+// grid = whole waves: num_sms x resident blocks per SM (capped by the number of site tiles)
+template <typename K>
+inline int wave_grid(K kernel, int threads, size_t smem, int num_sms, long tiles) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    long g = (long)per_sm * num_sms;
+    if (g > tiles) g = tiles;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <int P, int NR, int R, int EPI>
+inline cudaError_t launch_one(const KArgs &a, int threads, size_t smem, int num_sms, cudaStream_t stream, int *grid_out) {
+    auto k = dslash_kernel<P, NR, R, EPI>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    long tiles = (a.g.Vh + a.spb - 1) / a.spb;
+    int grid = wave_grid(k, threads, smem, num_sms, tiles);
+    if (grid_out) *grid_out = grid;
+    k<<<grid, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P, int NR, int EPI>
+inline cudaError_t launch_r(const KArgs &a, int R, int threads, size_t smem, int num_sms, cudaStream_t s, int *grid) {
+    switch (R) {
+    case 1: return launch_one<P, NR, 1, EPI>(a, threads, smem, num_sms, s, grid);
+    case 2: return launch_one<P, NR, 2, EPI>(a, threads, smem, num_sms, s, grid);
+    case 4: return launch_one<P, NR, 4, EPI>(a, threads, smem, num_sms, s, grid);
+    default: return launch_one<P, NR, 8, EPI>(a, threads, smem, num_sms, s, grid);
+    }
+}
+
+template <int P, int NR>
+inline cudaError_t launch_epi(const KArgs &a, int epi, int R, int threads, size_t smem, int num_sms, cudaStream_t s, int *grid) {
+    if (epi == EPI_PLAIN) return launch_r<P, NR, EPI_PLAIN>(a, R, threads, smem, num_sms, s, grid);
+    if constexpr (P == HISQ_FP64 && NR == 18) {
+        if (epi == EPI_RESID) return launch_r<P, NR, EPI_RESID>(a, R, threads, smem, num_sms, s, grid);
+    }
+    return launch_r<P, NR, EPI_AOP>(a, R, threads, smem, num_sms, s, grid);
+}
+
+// The per-precision entry (defined in dslash_<prec>.cu).
+template <int P>
+cudaError_t launch_dslash_prec(const KArgs &a, int recon, int epi, int R, int threads, size_t smem,
+                               int num_sms, cudaStream_t s, int *grid);
+
+}  // namespace hisq

@@ -1,0 +1,719 @@
+// Conjugate-gradient solvers on A = m^2 - D_eo D_oe (rows a3-a6, a9): fused masked BLAS-1
+// kernels with FP64 bundle reductions, device-side per-right-hand-side control (hooks), FP64
+// reliable updates, and two drivers: host-driven iterations (residual flags read back every
+// check_every iterations, as the per-iteration residual transfer of Sec. 2) and a single
+// captured CUDA graph whose WHILE/IF conditional nodes keep the whole solve on the device.
+#include <string.h>
+#include <math.h>
+#include <chrono>
+#include <algorithm>
+
+#include "hisq_internal.cuh"
+#include "dslash_kernel.cuh"
+
+namespace hisq {
+
+// Sloppy (Dslash) precision P and the precision Q of the iterated x and r.
+__host__ __device__ constexpr int q_prec(int p) { return p == HISQ_FP64 ? HISQ_FP64 : HISQ_FP32; }
+
+struct BlasArgs {
+    int Vh, n, spb;
+    void *x;          // Q: x_lo
+    void *r;          // Q: r_lo
+    void *p;          // P
+    void *Ap;         // P
+    void *z;          // P (flexible CG: preconditioned residual) or null
+    void *r_old;      // Q (flexible CG)
+    const void *b;    // FP64 (init)
+    void *xhi;        // FP64
+    RedArgs red;
+    SolverState *st;
+    const int *gate;
+};
+
+template <int P>
+__device__ __forceinline__ float site_scale(const VecView<P> &v, int s, int r) {
+    if constexpr (P == HISQ_FP16) return v.scale[(long)s * v.n + r];
+    return 1.0f;
+}
+
+template <int P>
+__device__ __forceinline__ void load3(const VecView<P> &v, int s, int r, Cplx<typename Prec<P>::real> w[3]) {
+    float sc = site_scale<P>(v, s, r);
+#pragma unroll
+    for (int c = 0; c < 3; c++) w[c] = load_elem<P>(v, ((long)s * 3 + c) * v.n + r, sc);
+}
+
+// one thread per (site, rhs); red rows = sites per block
+#define BLAS_PROLOGUE                                        \
+    const int tid = threadIdx.x;                             \
+    const int r = tid % a.n;                                 \
+    const int sl = tid / a.n;
+
+// init: x_hi = 0, x_lo = 0, r_lo = b, p = b, |b|^2 -> HOOK_INIT
+template <int P>
+__global__ void __launch_bounds__(256) cg_init_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    using rq = typename Prec<Q>::real;
+    extern __shared__ double red[];
+    BLAS_PROLOGUE
+    auto vb = view<HISQ_FP64>(a.b, a.Vh, a.n);
+    auto vxh = view<HISQ_FP64>(a.xhi, a.Vh, a.n);
+    auto vx = view<Q>(a.x, a.Vh, a.n);
+    auto vr = view<Q>(a.r, a.Vh, a.n);
+    auto vp = view<P>(a.p, a.Vh, a.n);
+    double acc = 0.0;
+    for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+        int s = tile * a.spb + sl;
+        if (s >= a.Vh || sl >= a.spb) continue;
+        Cplx<double> b[3];
+        load3<HISQ_FP64>(vb, s, r, b);
+        Cplx<double> zero[3] = {{0, 0}, {0, 0}, {0, 0}};
+        Cplx<rq> bq[3], zq[3] = {{0, 0}, {0, 0}, {0, 0}};
+        Cplx<typename Prec<P>::real> bp[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            acc += b[c].re * b[c].re + b[c].im * b[c].im;
+            bq[c] = {(rq)b[c].re, (rq)b[c].im};
+            bp[c] = {(typename Prec<P>::real)b[c].re, (typename Prec<P>::real)b[c].im};
+        }
+        store_site<HISQ_FP64>(vxh, s, r, zero);
+        store_site<Q>(vx, s, r, zq);
+        store_site<Q>(vr, s, r, bq);
+        store_site<P>(vp, s, r, bp);
+    }
+    const int rows = blockDim.x / a.n;
+    for (int i = tid; i < rows * a.n; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (sl < rows) red[sl * a.n + r] = acc;
+    block_reduce_finish(red, rows, a.n, a.n, a.red);
+}
+
+// x_lo += alpha p; r_lo -= alpha Ap; |r|^2 -> HOOK_DECIDE   (alpha complex for flexible CG)
+template <int P>
+__global__ void __launch_bounds__(256) cg_update_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    using rq = typename Prec<Q>::real;
+    extern __shared__ double red[];
+    BLAS_PROLOGUE
+    auto vx = view<Q>(a.x, a.Vh, a.n);
+    auto vr = view<Q>(a.r, a.Vh, a.n);
+    auto vp = view<P>(a.p, a.Vh, a.n);
+    auto vap = view<P>(a.Ap, a.Vh, a.n);
+    const bool act = a.st->active[r] != 0;
+    const rq al_re = (rq)a.st->alpha[r][0], al_im = (rq)a.st->alpha[r][1];
+    double acc = 0.0;
+    if (act) {
+        for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+            int s = tile * a.spb + sl;
+            if (s >= a.Vh || sl >= a.spb) continue;
+            Cplx<typename Prec<P>::real> p[3], ap[3];
+            Cplx<rq> x[3], rv[3];
+            load3<P>(vp, s, r, p);
+            load3<P>(vap, s, r, ap);
+            load3<Q>(vx, s, r, x);
+            load3<Q>(vr, s, r, rv);
+            rq part = 0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                x[c].re += al_re * (rq)p[c].re - al_im * (rq)p[c].im;
+                x[c].im += al_re * (rq)p[c].im + al_im * (rq)p[c].re;
+                rv[c].re -= al_re * (rq)ap[c].re - al_im * (rq)ap[c].im;
+                rv[c].im -= al_re * (rq)ap[c].im + al_im * (rq)ap[c].re;
+                part += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+            }
+            acc += (double)part;
+            store_site<Q>(vx, s, r, x);
+            store_site<Q>(vr, s, r, rv);
+        }
+    }
+    const int rows = blockDim.x / a.n;
+    for (int i = tid; i < rows * a.n; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (sl < rows) red[sl * a.n + r] = acc;
+    block_reduce_finish(red, rows, a.n, a.n, a.red);
+}
+
+// p = r + beta p for active right-hand sides (plain CG) -> HOOK_LOOP
+template <int P>
+__global__ void __launch_bounds__(256) cg_pupdate_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    using rp = typename Prec<P>::real;
+    extern __shared__ double red[];
+    BLAS_PROLOGUE
+    auto vr = view<Q>(a.r, a.Vh, a.n);
+    auto vp = view<P>(a.p, a.Vh, a.n);
+    const bool act = a.st->active[r] != 0;
+    const rp be = (rp)a.st->beta[r][0];
+    if (act) {
+        for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+            int s = tile * a.spb + sl;
+            if (s >= a.Vh || sl >= a.spb) continue;
+            Cplx<typename Prec<Q>::real> rv[3];
+            Cplx<rp> p[3];
+            load3<Q>(vr, s, r, rv);
+            load3<P>(vp, s, r, p);
+#pragma unroll
+            for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
+            store_site<P>(vp, s, r, p);
+        }
+    }
+    block_reduce_finish(red, 1, 0, a.n, a.red);
+}
+
+// reliable update, first step: x_hi += x_lo; x_lo = 0 for right-hand sides flagged for update
+template <int P>
+__global__ void __launch_bounds__(256) cg_xhi_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    if (a.gate && *a.gate == 0) return;
+    BLAS_PROLOGUE
+    if (!a.st->update[r]) return;
+    auto vx = view<Q>(a.x, a.Vh, a.n);
+    auto vxh = view<HISQ_FP64>(a.xhi, a.Vh, a.n);
+    for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+        int s = tile * a.spb + sl;
+        if (s >= a.Vh || sl >= a.spb) continue;
+        Cplx<typename Prec<Q>::real> x[3];
+        Cplx<double> xh[3];
+        load3<Q>(vx, s, r, x);
+        load3<HISQ_FP64>(vxh, s, r, xh);
+        Cplx<typename Prec<Q>::real> zero[3] = {{0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+        for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
+        store_site<HISQ_FP64>(vxh, s, r, xh);
+        store_site<Q>(vx, s, r, zero);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Workspace
+// ------------------------------------------------------------------------------------------
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const hisq_links *fat = nullptr, *naik = nullptr;
+    const hisq_pc *pc = nullptr;
+    double mass = 0;
+    int n = 0, prec = -1;
+};
+
+struct Workspace {
+    int cap_n = 0;
+    int prec = -1;
+    void *b_hi = nullptr, *x_hi = nullptr, *x_lo = nullptr, *r_lo = nullptr, *p = nullptr, *Ap = nullptr;
+    void *t = nullptr, *t64 = nullptr, *z = nullptr, *r_old = nullptr;
+    double *canon = nullptr;      // canonical FP64 staging [cap_n][Vh][6]
+    SolverState *st = nullptr;    // device
+    SolverState *h_st = nullptr;  // pinned host mirror
+    double *partials = nullptr;
+    size_t partials_cap = 0;
+    unsigned int *counter = nullptr;
+    double *dots = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    GraphCache gc;
+};
+
+void free_graph(GraphCache &gc) {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    if (gc.graph) cudaGraphDestroy(gc.graph);
+    gc = GraphCache();
+}
+
+static void free_buffers(Workspace *w) {
+    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->canon};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = nullptr;
+    w->canon = nullptr;
+    w->cap_n = 0;
+    w->prec = -1;
+    free_graph(w->gc);
+}
+
+static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
+    if (!ctx->ws) {
+        Workspace *w = new Workspace();
+        ctx->ws = w;
+        size_t pcap = (size_t)ctx->num_sms * 64 * HISQ_MAX_BUNDLE * 4;
+        if (cudaMalloc(&w->st, sizeof(SolverState)) != cudaSuccess ||
+            cudaMallocHost(&w->h_st, sizeof(SolverState)) != cudaSuccess ||
+            cudaMalloc(&w->partials, pcap * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&w->counter, sizeof(unsigned int) * 4) != cudaSuccess ||
+            cudaMalloc(&w->dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) != cudaSuccess)
+            return set_error(HISQ_ERR_NOMEM, "solver workspace allocation failed");
+        w->partials_cap = pcap;
+        cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
+        memset(w->h_st, 0, sizeof(SolverState));
+        cudaEventCreate(&w->ev0);
+        cudaEventCreate(&w->ev1);
+    }
+    Workspace *w = ctx->ws;
+    bool have_pc = w->z != nullptr;
+    if (w->cap_n >= n && w->prec == prec && (!need_pc || have_pc)) return HISQ_OK;
+    int cap = std::max(n, w->cap_n);
+    free_buffers(w);
+    int Vh = ctx->geom.Vh;
+    int Q = q_prec(prec);
+    struct { void **ptr; size_t bytes; } allocs[] = {
+        {&w->b_hi, vector_bytes(HISQ_FP64, Vh, cap)}, {&w->x_hi, vector_bytes(HISQ_FP64, Vh, cap)},
+        {&w->x_lo, vector_bytes(Q, Vh, cap)},         {&w->r_lo, vector_bytes(Q, Vh, cap)},
+        {&w->p, vector_bytes(prec, Vh, cap)},         {&w->Ap, vector_bytes(prec, Vh, cap)},
+        {&w->t, vector_bytes(prec, Vh, cap)},         {&w->t64, vector_bytes(HISQ_FP64, Vh, cap)},
+        {(void **)&w->canon, (size_t)cap * Vh * 6 * sizeof(double)},
+    };
+    for (auto &a : allocs)
+        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+            free_buffers(w);
+            return set_error(HISQ_ERR_NOMEM, "cannot allocate %zu bytes of solver workspace", a.bytes);
+        }
+    if (need_pc) {
+        if (cudaMalloc(&w->z, vector_bytes(prec, Vh, cap)) != cudaSuccess ||
+            cudaMalloc(&w->r_old, vector_bytes(Q, Vh, cap)) != cudaSuccess) {
+            free_buffers(w);
+            return set_error(HISQ_ERR_NOMEM, "cannot allocate flexible-CG workspace");
+        }
+    }
+    w->cap_n = cap;
+    w->prec = prec;
+    return HISQ_OK;
+}
+
+void free_workspace(hisq_ctx *ctx) {
+    if (!ctx->ws) return;
+    Workspace *w = ctx->ws;
+    free_buffers(w);
+    if (w->st) cudaFree(w->st);
+    if (w->h_st) cudaFreeHost(w->h_st);
+    if (w->partials) cudaFree(w->partials);
+    if (w->counter) cudaFree(w->counter);
+    if (w->dots) cudaFree(w->dots);
+    if (w->ev0) cudaEventDestroy(w->ev0);
+    if (w->ev1) cudaEventDestroy(w->ev1);
+    delete w;
+    ctx->ws = nullptr;
+}
+
+// ------------------------------------------------------------------------------------------
+// Enqueueing the steps of one bundle solve
+// ------------------------------------------------------------------------------------------
+struct Solve {
+    hisq_ctx *ctx;
+    Workspace *w;
+    const hisq_links *fat, *naik;
+    int n, prec;
+    double mass;
+    cudaStream_t st;
+    bool timing;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events;
+};
+
+static BlasArgs blas_args(const Solve &S) {
+    BlasArgs a;
+    memset(&a, 0, sizeof(a));
+    a.Vh = S.ctx->geom.Vh;
+    a.n = S.n;
+    a.spb = std::max(1, 256 / S.n);
+    int p2 = 1;
+    while (p2 * 2 <= a.spb) p2 *= 2;
+    a.spb = p2;
+    a.x = S.w->x_lo;
+    a.r = S.w->r_lo;
+    a.p = S.w->p;
+    a.Ap = S.w->Ap;
+    a.z = S.w->z;
+    a.r_old = S.w->r_old;
+    a.b = S.w->b_hi;
+    a.xhi = S.w->x_hi;
+    a.red.partials = S.w->partials;
+    a.red.counter = S.w->counter;
+    a.red.dot_out = S.w->dots;
+    a.red.st = S.w->st;
+    a.st = S.w->st;
+    return a;
+}
+
+template <typename K>
+static int launch_blas(const Solve &S, K kernel, BlasArgs a, int hook, bool reduce) {
+    int threads = a.spb * a.n;
+    size_t smem = reduce ? (size_t)std::max(threads, a.spb * a.n) * sizeof(double) : 0;
+    long tiles = (a.Vh + a.spb - 1) / a.spb;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    long grid = std::min<long>(tiles, (long)std::max(per_sm, 1) * S.ctx->num_sms);
+    if ((size_t)grid * a.n * 2 > S.w->partials_cap) grid = S.w->partials_cap / (a.n * 2);
+    a.red.hook = hook;
+    kernel<<<(int)grid, threads, smem, S.st>>>(a);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
+}
+
+template <int P>
+static int enqueue_blas(const Solve &S, int which) {
+    BlasArgs a = blas_args(S);
+    switch (which) {
+    case HOOK_INIT: return launch_blas(S, cg_init_kernel<P>, a, HOOK_INIT, true);
+    case HOOK_DECIDE: return launch_blas(S, cg_update_kernel<P>, a, HOOK_DECIDE, true);
+    case HOOK_LOOP: return launch_blas(S, cg_pupdate_kernel<P>, a, HOOK_LOOP, true);
+    default: {
+        a.gate = &S.w->st->any_update;
+        return launch_blas(S, cg_xhi_kernel<P>, a, HOOK_NONE, false);
+    }
+    }
+}
+
+static int blas(const Solve &S, int which) {
+    switch (S.prec) {
+    case HISQ_FP64: return enqueue_blas<HISQ_FP64>(S, which);
+    case HISQ_FP32: return enqueue_blas<HISQ_FP32>(S, which);
+    case HISQ_FP16: return enqueue_blas<HISQ_FP16>(S, which);
+    default: return enqueue_blas<HISQ_BF16>(S, which);
+    }
+}
+
+static int dslash_step(const Solve &S, DslashArgs d, bool use64) {
+    d.partials = S.w->partials;
+    d.partials_cap = S.w->partials_cap;
+    d.counter = S.w->counter;
+    d.dot_out = S.w->dots;
+    d.hook_state = S.w->st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (S.timing) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, S.st);
+    }
+    int rc = launch_dslash(S.ctx, S.fat, S.naik, use64, d, nullptr, S.st);
+    if (S.timing) {
+        cudaEventRecord(e1, S.st);
+        S.events->push_back({e0, e1});
+    }
+    return rc;
+}
+
+// the reliable update: x_hi += x_lo; t64 = D_oe x_hi; r_lo = b - A x_hi (FP64) -> HOOK_RELIABLE
+static int enqueue_update(const Solve &S) {
+    HISQ_CHECK(blas(S, -1));
+    DslashArgs d;
+    memset(&d, 0, sizeof(d));
+    d.n = S.n;
+    d.in = S.w->x_hi;
+    d.out = S.w->t64;
+    d.parity = 1;
+    d.epi = EPI_PLAIN;
+    d.active = S.w->st->update;
+    d.gate = &S.w->st->any_update;
+    HISQ_CHECK(dslash_step(S, d, true));
+    d.in = S.w->t64;
+    d.out = nullptr;
+    d.parity = 0;
+    d.epi = EPI_RESID;
+    d.mass2 = S.mass * S.mass;
+    d.axpy_in = S.w->x_hi;
+    d.b = S.w->b_hi;
+    d.out_lo = S.w->r_lo;
+    d.lo_prec = q_prec(S.prec);
+    d.hook = HOOK_RELIABLE;
+    return dslash_step(S, d, true);
+}
+
+// one CG iteration up to the decision: t = D_oe p; Ap = m^2 p - D_eo t (pAp -> alpha);
+// x += alpha p, r -= alpha Ap (|r|^2 -> decide)
+static int enqueue_iteration_head(const Solve &S) {
+    DslashArgs d;
+    memset(&d, 0, sizeof(d));
+    d.n = S.n;
+    d.in = S.w->p;
+    d.out = S.w->t;
+    d.parity = 1;
+    d.epi = EPI_PLAIN;
+    d.active = S.w->st->active;
+    HISQ_CHECK(dslash_step(S, d, false));
+    d.in = S.w->t;
+    d.out = S.w->Ap;
+    d.parity = 0;
+    d.epi = EPI_AOP;
+    d.mass2 = S.mass * S.mass;
+    d.axpy_in = S.w->p;
+    d.hook = HOOK_ALPHA;
+    HISQ_CHECK(dslash_step(S, d, false));
+    return blas(S, HOOK_DECIDE);
+}
+
+static int enqueue_setup(const Solve &S) {
+    // b_hi from the canonical staging, then x = 0, r = p = b and |b|^2
+    HISQ_CHECK(pack_vectors(S.ctx, S.w->canon, S.w->b_hi, S.n, HISQ_FP64, S.st));
+    return blas(S, HOOK_INIT);
+}
+
+static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol) {
+    const hisq_solver_params &P = S.ctx->params;
+    SolverState *h = S.w->h_st;
+    memset(h, 0, sizeof(SolverState));
+    h->n = S.n;
+    h->max_iter = P.max_iter;
+    h->inner_fp64 = S.prec == HISQ_FP64;
+    h->use_pc = 0;
+    h->stall_window = P.stall_window;
+    h->stall_factor = P.stall_factor;
+    h->tol = tol;
+    h->delta = P.delta;
+    h->h_loop = h_loop;
+    h->h_upd = h_upd;
+    HISQ_CUDA(cudaMemcpyAsync(S.w->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, S.st));
+    return HISQ_OK;
+}
+
+// ---- graph capture with conditional nodes ----------------------------------------------------
+static int add_conditional(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                           cudaGraph_t *body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps;
+    const cudaGraphEdgeData *edges;
+    size_t ndeps;
+    HISQ_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return set_error(HISQ_ERR_CUDA, "stream is not capturing");
+    cudaGraphNodeParams params = {cudaGraphNodeTypeConditional};
+    params.conditional.handle = h;
+    params.conditional.type = type;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    HISQ_CUDA(cudaGraphAddNode(&node, g, deps, edges, ndeps, &params));
+    *body = params.conditional.phGraph_out[0];
+    HISQ_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return HISQ_OK;
+}
+
+static int build_graph(const Solve &S) {
+    Workspace *w = S.w;
+    free_graph(w->gc);
+    cudaGraph_t graph;
+    HISQ_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h_loop, h_upd;
+    HISQ_CUDA(cudaGraphConditionalHandleCreate(&h_loop, graph, 1, cudaGraphCondAssignDefault));
+    HISQ_CUDA(cudaGraphConditionalHandleCreate(&h_upd, graph, 0, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    HISQ_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = HISQ_OK;
+    Solve C = S;
+    C.st = cap;
+    C.timing = false;
+    // the state parameters (including the handles) are copied before the graph launch, so the
+    // graph itself only holds: setup; WHILE(loop) { head; IF(update) { update }; p-update }
+    w->h_st->h_loop = (unsigned long long)h_loop;
+    w->h_st->h_upd = (unsigned long long)h_upd;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraph_t while_body = nullptr;
+    if (rc == HISQ_OK) rc = enqueue_setup(C);
+    if (rc == HISQ_OK) rc = add_conditional(cap, h_loop, cudaGraphCondTypeWhile, &while_body);
+    cudaGraph_t outg;
+    e = cudaStreamEndCapture(cap, &outg);
+    if (rc == HISQ_OK && e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    // WHILE body: head; IF node; p-update
+    cudaGraph_t if_body = nullptr;
+    if (rc == HISQ_OK) {
+        e = cudaStreamBeginCaptureToGraph(cap, while_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "loop capture failed: %s", cudaGetErrorString(e));
+        if (rc == HISQ_OK) rc = enqueue_iteration_head(C);
+        if (rc == HISQ_OK) rc = add_conditional(cap, h_upd, cudaGraphCondTypeIf, &if_body);
+        if (rc == HISQ_OK) rc = blas(C, HOOK_LOOP);
+        e = cudaStreamEndCapture(cap, &outg);
+        if (rc == HISQ_OK && e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "loop capture failed: %s", cudaGetErrorString(e));
+    }
+    if (rc == HISQ_OK) {
+        e = cudaStreamBeginCaptureToGraph(cap, if_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "update capture failed: %s", cudaGetErrorString(e));
+        if (rc == HISQ_OK) rc = enqueue_update(C);
+        e = cudaStreamEndCapture(cap, &outg);
+        if (rc == HISQ_OK && e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "update capture failed: %s", cudaGetErrorString(e));
+    }
+    cudaStreamDestroy(cap);
+    if (rc == HISQ_OK) {
+        e = cudaGraphInstantiate(&w->gc.exec, graph, 0);
+        if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    if (rc != HISQ_OK) {
+        cudaGraphDestroy(graph);
+        w->gc = GraphCache();
+        cudaGetLastError();
+        return rc;
+    }
+    w->gc.graph = graph;
+    w->gc.fat = S.fat;
+    w->gc.naik = S.naik;
+    w->gc.mass = S.mass;
+    w->gc.n = S.n;
+    w->gc.prec = S.prec;
+    w->gc.pc = nullptr;
+    return HISQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// One bundle
+// ------------------------------------------------------------------------------------------
+static int solve_bundle(Solve &S, double tol) {
+    Workspace *w = S.w;
+    const hisq_solver_params &P = S.ctx->params;
+    bool graph = P.use_graph && !S.timing;
+    if (graph) {
+        bool reuse = w->gc.exec && w->gc.fat == S.fat && w->gc.naik == S.naik && w->gc.mass == S.mass &&
+                     w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == nullptr;
+        unsigned long long hl = w->h_st->h_loop, hu = w->h_st->h_upd;
+        if (!reuse) {
+            HISQ_CHECK(build_graph(S));
+            hl = w->h_st->h_loop;
+            hu = w->h_st->h_upd;
+        }
+        HISQ_CHECK(set_state_params(S, hl, hu, tol));
+        HISQ_CUDA(cudaGraphLaunch(w->gc.exec, S.st));
+        HISQ_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(SolverState), cudaMemcpyDeviceToHost, S.st));
+        HISQ_CUDA(cudaStreamSynchronize(S.st));
+        w->h_st->h_loop = hl;
+        w->h_st->h_upd = hu;
+        return HISQ_OK;
+    }
+    HISQ_CHECK(set_state_params(S, 0, 0, tol));
+    HISQ_CHECK(enqueue_setup(S));
+    int check = std::max(1, P.check_every);
+    for (int it = 0; it < P.max_iter; it++) {
+        HISQ_CHECK(enqueue_iteration_head(S));
+        HISQ_CHECK(enqueue_update(S));
+        HISQ_CHECK(blas(S, HOOK_LOOP));
+        if ((it + 1) % check == 0 || it + 1 == P.max_iter) {
+            // the per-iteration residual/flag read-back
+            HISQ_CUDA(cudaMemcpyAsync(&w->h_st->any_active, &w->st->any_active, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+            HISQ_CUDA(cudaStreamSynchronize(S.st));
+            if (!w->h_st->any_active) break;
+        }
+    }
+    HISQ_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(SolverState), cudaMemcpyDeviceToHost, S.st));
+    HISQ_CUDA(cudaStreamSynchronize(S.st));
+    return HISQ_OK;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+int hisq_set_solver_params(const hisq_solver_params *p) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!p) return set_error(HISQ_ERR_ARG, "null params");
+    if (p->inner_prec < HISQ_FP64 || p->inner_prec > HISQ_BF16) return set_error(HISQ_ERR_ARG, "bad inner precision");
+    if (p->max_iter < 1) return set_error(HISQ_ERR_ARG, "max_iter must be >= 1");
+    if (!(p->delta > 0.0 && p->delta < 1.0)) return set_error(HISQ_ERR_ARG, "delta must be in (0, 1)");
+    if (p->bundle < 0 || p->bundle > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "bundle must be in 0..%d", HISQ_MAX_BUNDLE);
+    if (p->pc && p->pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
+    ctx->params = *p;
+    return HISQ_OK;
+}
+
+int hisq_get_solver_params(hisq_solver_params *p) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!p) return set_error(HISQ_ERR_ARG, "null params");
+    *p = ctx->params;
+    return HISQ_OK;
+}
+
+int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *const rhs[], double *x[], int nrhs,
+                  double mass, double tol) {
+    auto t0 = std::chrono::steady_clock::now();
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!fat || !naik || !rhs || !x) return set_error(HISQ_ERR_ARG, "null argument");
+    if (fat->ctx != ctx || naik->ctx != ctx) return set_error(HISQ_ERR_STATE, "links of another context");
+    if (fat->is_naik || !naik->is_naik) return set_error(HISQ_ERR_ARG, "expected (fat, naik) links");
+    if (nrhs < 1) return set_error(HISQ_ERR_ARG, "nrhs must be >= 1");
+    if (!(tol > 0.0)) return set_error(HISQ_ERR_ARG, "tol must be positive");
+    for (int k = 0; k < nrhs; k++)
+        if (!rhs[k] || !x[k]) return set_error(HISQ_ERR_ARG, "null rhs or x pointer %d", k);
+    const hisq_solver_params &P = ctx->params;
+    int prec = P.inner_prec;
+    if (prec != HISQ_FP64 && fat->prec != prec)
+        return set_error(HISQ_ERR_ARG, "inner precision %d needs links packed in that precision (links are %d)", prec, fat->prec);
+    if (fat->prec != naik->prec) return set_error(HISQ_ERR_ARG, "fat and Naik links have different precisions");
+    if (P.pc) return set_error(HISQ_ERR_ARG, "flexible CG is driven by hisq_fcg (preconditioner set)");
+    int bundle = P.bundle > 0 ? P.bundle : std::min(nrhs, HISQ_MAX_BUNDLE);
+    bundle = std::min(bundle, nrhs);
+    HISQ_CHECK(ensure_workspace(ctx, bundle, prec, false));
+    Workspace *w = ctx->ws;
+    const int Vh = ctx->geom.Vh;
+    const size_t vbytes = (size_t)Vh * 6 * sizeof(double);
+
+    ctx->stat_iters.assign(nrhs, 0);
+    ctx->stat_resid.assign(nrhs, 1.0);
+    hisq_solve_stats &stats = ctx->stats;
+    memset(&stats, 0, sizeof(stats));
+    stats.nrhs = nrhs;
+    stats.bundle_size = bundle;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    int worst = HISQ_OK;
+
+    for (int k0 = 0; k0 < nrhs; k0 += bundle) {
+        int n = std::min(bundle, nrhs - k0);
+        Solve S{ctx, w, fat, naik, n, prec, mass, ctx->stream, P.time_kernels != 0, &events};
+        // tune (outside any capture) before the first use of this shape
+        if (P.autotune) {
+            tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64);
+            tuned_shape(ctx, fat, naik, n, true);
+        }
+        for (int k = 0; k < n; k++)
+            HISQ_CUDA(cudaMemcpyAsync(w->canon + (size_t)k * Vh * 6, rhs[k0 + k], vbytes, cudaMemcpyDefault, ctx->stream));
+        HISQ_CHECK(solve_bundle(S, tol));
+        HISQ_CHECK(unpack_vectors(ctx, w->x_hi, w->canon, n, HISQ_FP64, ctx->stream));
+        for (int k = 0; k < n; k++)
+            HISQ_CUDA(cudaMemcpyAsync(x[k0 + k], w->canon + (size_t)k * Vh * 6, vbytes, cudaMemcpyDefault, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        const SolverState &h = *w->h_st;
+        int bmax = 0;
+        for (int k = 0; k < n; k++) {
+            ctx->stat_iters[k0 + k] = h.iters[k];
+            ctx->stat_resid[k0 + k] = h.true_res[k];
+            stats.total_iterations += h.iters[k];
+            stats.max_iterations = std::max(stats.max_iterations, h.iters[k]);
+            stats.reliable_updates += h.updates[k];
+            bmax = std::max(bmax, h.iters[k]);
+            stats.flops += (double)h.iters[k] * Vh * (2.0 * 1146 + 72);
+            if (h.status[k] == RHS_CONVERGED) stats.converged++;
+            else if (h.status[k] == RHS_BREAKDOWN) worst = HISQ_ERR_BREAKDOWN;
+            else if (worst == HISQ_OK) worst = HISQ_ERR_NOT_CONVERGED;
+        }
+        stats.fallbacks += h.fallbacks;
+        stats.bundle_iterations += bmax;
+        stats.bundles++;
+    }
+    for (auto &e : events) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+            stats.dslash_ms += ms;
+            stats.dslash_launches++;
+        }
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (worst == HISQ_ERR_NOT_CONVERGED)
+        return set_error(worst, "%d of %d right-hand sides missed tol %.1e within %d iterations", nrhs - stats.converged,
+                         nrhs, tol, P.max_iter);
+    if (worst == HISQ_ERR_BREAKDOWN) return set_error(worst, "solver breakdown in at least one right-hand side");
+    return HISQ_OK;
+}
+
+int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!s) return set_error(HISQ_ERR_ARG, "null stats");
+    *s = ctx->stats;
+    int n = (int)ctx->stat_iters.size();
+    if (iterations)
+        for (int k = 0; k < n; k++) iterations[k] = ctx->stat_iters[k];
+    if (true_residual)
+        for (int k = 0; k < n; k++) true_residual[k] = ctx->stat_resid[k];
+    return HISQ_OK;
+}
+
+}  // extern "C"

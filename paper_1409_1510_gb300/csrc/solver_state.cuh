@@ -1,0 +1,213 @@
+// Device-resident per-bundle solver state and the scalar steps ("hooks") that the last block of
+// a reducing kernel runs once the bundle-wide dot products are complete.
+#pragma once
+#include "hisq_internal.cuh"
+
+namespace hisq {
+
+enum RhsStatus { RHS_RUNNING = 0, RHS_CONVERGED = 1, RHS_NOT_CONVERGED = 2, RHS_BREAKDOWN = 3 };
+
+enum Hook {
+    HOOK_NONE = 0,
+    HOOK_INIT = 1,      // dots = |b|^2: set up norms and masks
+    HOOK_ALPHA = 2,     // dots = <p, A p>: alpha = rr / pAp          (plain CG)
+    HOOK_DECIDE = 3,    // dots = |r|^2 after the update: beta or reliable update
+    HOOK_RELIABLE = 4,  // dots = |b - A x_hi|^2 (FP64): convergence, restart of r
+    HOOK_LOOP = 5,      // no dots: advance the iteration counter, set the loop condition
+    HOOK_FCG_ALPHA = 6, // dots = <p, A p>, <p, r> (complex): alpha for flexible CG
+    HOOK_FCG_BETA = 7,  // dots = <r - r_old, z>, <r, z>: beta for flexible CG
+};
+
+struct SolverState {
+    double rr[HISQ_MAX_BUNDLE];       // |r|^2 of the iterated residual
+    double rr_prev[HISQ_MAX_BUNDLE];  // |r|^2 one iteration earlier
+    double alpha[HISQ_MAX_BUNDLE][2]; // complex (imaginary part 0 for plain CG)
+    double beta[HISQ_MAX_BUNDLE][2];
+    double rp_old[HISQ_MAX_BUNDLE][2];// flexible CG: <r_{k-1}, p_{k-1}>
+    double r_upd[HISQ_MAX_BUNDLE];    // |r| at the last FP64 residual recomputation
+    double r_win[HISQ_MAX_BUNDLE];    // flexible CG: |r| at the start of the stall window
+    double bnorm[HISQ_MAX_BUNDLE];
+    double true_res[HISQ_MAX_BUNDLE]; // last FP64 relative true residual
+    int active[HISQ_MAX_BUNDLE];      // 1 while iterating
+    int update[HISQ_MAX_BUNDLE];      // 1 when an FP64 residual recomputation is due
+    int iters[HISQ_MAX_BUNDLE];
+    int updates[HISQ_MAX_BUNDLE];
+    int status[HISQ_MAX_BUNDLE];
+    int win_start[HISQ_MAX_BUNDLE];   // flexible CG: iteration where the stall window began
+    int fallback[HISQ_MAX_BUNDLE];    // flexible CG: 1 once switched to plain CG
+    int fallbacks;
+    int any_update;
+    int any_active;
+    int bundle_iters;
+    int n;
+    int max_iter;
+    int inner_fp64;                   // 1: iterated residual is FP64 (update only at tol)
+    int use_pc;
+    int stall_window;
+    double stall_factor;
+    double tol;
+    double delta;
+    unsigned long long h_loop;        // conditional handles (0 when not in a graph)
+    unsigned long long h_upd;
+};
+
+__device__ __forceinline__ void set_condition(unsigned long long handle, unsigned int value) {
+    if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, value);
+}
+
+// Scalar step of the solver for one bundle.  Called by thread 0 of the last block of a reducing
+// kernel after the bundle-wide dots are final (dots[k] for right-hand side k; complex dots use
+// dots[2k], dots[2k+1]; HOOK_FCG_BETA has a second array of n complex dots after the first).
+__device__ __forceinline__ void run_hook(int hook, SolverState *st, const double *dots, int n) {
+    switch (hook) {
+    case HOOK_INIT: {
+        int any = 0;
+        for (int k = 0; k < n; k++) {
+            double b2 = dots[k];
+            st->bnorm[k] = sqrt(b2);
+            st->rr[k] = b2;
+            st->rr_prev[k] = b2;
+            st->r_upd[k] = sqrt(b2);
+            st->r_win[k] = sqrt(b2);
+            st->win_start[k] = 0;
+            st->fallback[k] = 0;
+            st->iters[k] = 0;
+            st->updates[k] = 0;
+            st->update[k] = 0;
+            st->alpha[k][0] = st->alpha[k][1] = 0.0;
+            st->beta[k][0] = st->beta[k][1] = 0.0;
+            st->rp_old[k][0] = 1.0; st->rp_old[k][1] = 0.0;
+            bool ok = isfinite(b2);
+            st->active[k] = (ok && b2 > 0.0) ? 1 : 0;
+            st->status[k] = !ok ? RHS_BREAKDOWN : (b2 > 0.0 ? RHS_RUNNING : RHS_CONVERGED);
+            st->true_res[k] = (b2 > 0.0 || !ok) ? 1.0 : 0.0;
+            any |= st->active[k];
+        }
+        for (int k = n; k < HISQ_MAX_BUNDLE; k++) { st->active[k] = 0; st->update[k] = 0; }
+        st->fallbacks = 0;
+        st->any_active = any;
+        st->any_update = 0;
+        st->bundle_iters = 0;
+        break;
+    }
+    case HOOK_ALPHA: {
+        for (int k = 0; k < n; k++) {
+            if (!st->active[k]) continue;
+            double pap = dots[k];
+            if (!(pap > 0.0) || !isfinite(pap)) {
+                st->active[k] = 0;
+                st->status[k] = RHS_BREAKDOWN;
+                st->alpha[k][0] = 0.0;
+                continue;
+            }
+            st->alpha[k][0] = st->rr[k] / pap;
+            st->alpha[k][1] = 0.0;
+        }
+        break;
+    }
+    case HOOK_FCG_ALPHA: {
+        // dots[2k] = <p, A p> (real part), dots[2k+1] unused; dots[2n + 2k (+1)] = <p, r>
+        for (int k = 0; k < n; k++) {
+            if (!st->active[k]) continue;
+            double pap = dots[2 * k];
+            double pr_re = dots[2 * n + 2 * k], pr_im = dots[2 * n + 2 * k + 1];
+            if (!(pap > 0.0) || !isfinite(pap) || !isfinite(pr_re) || !isfinite(pr_im)) {
+                st->active[k] = 0;
+                st->status[k] = RHS_BREAKDOWN;
+                st->alpha[k][0] = st->alpha[k][1] = 0.0;
+                continue;
+            }
+            st->alpha[k][0] = pr_re / pap;
+            st->alpha[k][1] = pr_im / pap;
+            st->rp_old[k][0] = pr_re;   // <r, p> = conj(<p, r>)
+            st->rp_old[k][1] = -pr_im;
+        }
+        break;
+    }
+    case HOOK_DECIDE: {
+        int any = 0;
+        for (int k = 0; k < n; k++) {
+            st->update[k] = 0;
+            if (!st->active[k]) continue;
+            st->iters[k] += 1;
+            double rr = dots[k];
+            if (!isfinite(rr)) {
+                st->active[k] = 0;
+                st->status[k] = RHS_BREAKDOWN;
+                continue;
+            }
+            double rn = sqrt(rr);
+            bool at_tol = rn <= st->tol * st->bnorm[k];
+            bool drop = (!st->inner_fp64) && rn < st->delta * st->r_upd[k];
+            bool last = st->iters[k] >= st->max_iter;
+            if (at_tol || drop || last) {
+                st->update[k] = 1;
+                any = 1;
+            }
+            st->rr_prev[k] = st->rr[k];
+            st->beta[k][0] = rr / st->rr[k];
+            st->beta[k][1] = 0.0;
+            st->rr[k] = rr;
+            if (st->use_pc && !st->fallback[k]) {
+                // stall detection for flexible CG: the residual must drop by stall_factor
+                // within stall_window iterations, else continue as plain CG
+                if (rn * st->stall_factor <= st->r_win[k]) {
+                    st->r_win[k] = rn;
+                    st->win_start[k] = st->iters[k];
+                } else if (st->iters[k] - st->win_start[k] >= st->stall_window) {
+                    st->fallback[k] = 1;
+                    st->fallbacks += 1;
+                }
+            }
+        }
+        st->any_update = any;
+        set_condition(st->h_upd, any);
+        break;
+    }
+    case HOOK_RELIABLE: {
+        for (int k = 0; k < n; k++) {
+            if (!st->update[k]) continue;
+            double r2 = dots[k];
+            st->updates[k] += 1;
+            if (!isfinite(r2)) {
+                st->active[k] = 0;
+                st->status[k] = RHS_BREAKDOWN;
+                continue;
+            }
+            double rn = sqrt(r2);
+            st->true_res[k] = rn / st->bnorm[k];
+            if (st->true_res[k] <= st->tol) {
+                st->active[k] = 0;
+                st->status[k] = RHS_CONVERGED;
+            } else if (st->iters[k] >= st->max_iter) {
+                st->active[k] = 0;
+                st->status[k] = RHS_NOT_CONVERGED;
+            } else {
+                // restart the iterated residual from the true one; keep the search direction
+                // with beta = |r_true|^2 / |r_previous|^2 (Sleijpen & van der Vorst reliable update)
+                st->beta[k][0] = r2 / st->rr_prev[k];
+                st->beta[k][1] = 0.0;
+                st->rr[k] = r2;
+                st->r_upd[k] = rn;
+            }
+        }
+        break;
+    }
+    case HOOK_LOOP: {
+        int any = 0;
+        for (int k = 0; k < n; k++) {
+            st->update[k] = 0;
+            any |= st->active[k];
+        }
+        st->any_active = any;
+        st->any_update = 0;
+        st->bundle_iters += 1;
+        set_condition(st->h_loop, (any && st->bundle_iters < st->max_iter) ? 1u : 0u);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+}  // namespace hisq

@@ -1,0 +1,123 @@
+"""Dslash (rows a1-a3) on the GPU through the C ABI, element by element against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import hisq_inputs as hi
+from gpu_util import PREC_TOL, gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+# 8 x 10 x 8 x 6: V/2 = 1920 output sites, several site tiles plus a ragged last tile; the hops
+# +-1 and +-3 reach distinct sites in x, y and z.
+DIMS = (8, 10, 8, 6)
+CASES = [(0, 18), (1, 18), (1, 13), (1, 9), (2, 18), (2, 13), (2, 9), (3, 18), (3, 13), (3, 9)]
+
+
+def _rhs(lat, n, seed=0):
+    return np.stack([hi.gaussian_rhs(lat, seed + k) for k in range(n)])
+
+
+@pytest.mark.parametrize("prec,recon", CASES)
+@pytest.mark.parametrize("n", [1, 3, 4, 12, 16])
+def test_dslash_parity(prec, recon, n):
+    with gpu(DIMS, prec, recon) as g:
+        v = _rhs(g.lat, n)
+        vin = g.pack(v)
+        vout = g.bundle(n)
+        for parity in (0, 1):
+            g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, parity)
+            err = rel_err(g.unpack(vout, n), g.oracle.dslash_eo(v, parity))
+            assert err <= PREC_TOL[prec], (parity, err)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_every_launch_shape(prec):
+    """Each compiled right-hand-sides-per-thread variant and several block sizes agree."""
+    n = 8
+    with gpu(DIMS, prec, 18) as g:
+        v = _rhs(g.lat, n, 40)
+        want = g.oracle.dslash_eo(v, 1)
+        vin, vout = g.pack(v), g.bundle(n)
+        for R in (1, 2, 4, 8):
+            if prec == 0 and R == 8:
+                continue
+            for threads in (32, 96, 256):
+                g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads)
+                vout.zero_()
+                g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 1)
+                assert rel_err(g.unpack(vout, n), want) <= PREC_TOL[prec], (R, threads)
+
+
+def test_dslash_max_nrhs_and_single_site_row():
+    """HISQ_MAX_NRHS right-hand sides in one call, and the smallest lattice (4^4)."""
+    with gpu((4, 4, 4, 4), 1, 18) as g:
+        v = _rhs(g.lat, 64, 100)
+        vin, vout = g.pack(v), g.bundle(64)
+        g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, 64, 0)
+        assert rel_err(g.unpack(vout, 64), g.oracle.dslash_eo(v, 0)) <= 1e-5
+
+
+def test_dslash_zero_input_gives_zero():
+    with gpu(DIMS, 2, 18) as g:
+        v = np.zeros((2, g.lat.half_volume, 3), complex)
+        vin, vout = g.pack(v), g.bundle(2)
+        g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, 2, 0)
+        assert np.all(g.unpack(vout, 2) == 0)
+
+
+@pytest.mark.parametrize("prec,recon", CASES)
+def test_links_export_matches_gathered_links(prec, recon):
+    """Row a1: the packed links decode to X_{x,mu} and -X^dag_{x-mu,mu} (N with 3 hops) of the
+    canonical input, within the storage precision."""
+    dims = (8, 4, 6, 4)
+    with gpu(dims, prec, recon) as g:
+        lat = g.lat
+        c = lat.coords()
+        for handle, U, hop in ((g.fat, g.X, 1), (g.naik, g.N, 3)):
+            out = np.empty((2, lat.half_volume, 8, 3, 3, 2))
+            g.hisq.hisq_links_export(handle, out)
+            got = out.view(np.complex128)[..., 0]
+            for parity in (0, 1):
+                sites = lat.eo_sites(parity)
+                want = np.empty((lat.half_volume, 8, 3, 3), complex)
+                for mu in range(4):
+                    cc = c[sites].copy()
+                    cc[:, mu] = (cc[:, mu] - hop) % dims[mu]
+                    back = cc[:, 0] + dims[0] * (cc[:, 1] + dims[1] * (cc[:, 2] + dims[2] * cc[:, 3]))
+                    want[:, 2 * mu] = U[mu][sites]
+                    want[:, 2 * mu + 1] = -U[mu][back].conj().swapaxes(-1, -2)
+                scale = np.abs(want).max()
+                err = np.abs(got[parity] - want).max() / scale
+                # the 9-real encoding divides by |W01|^2 + |W02|^2, which is small for links near
+                # the identity (its singular point), so its rounding error is amplified
+                bound = {0: 1e-15, 1: 1e-6, 2: 2e-3, 3: 1e-2}[prec] * {18: 1, 13: 10, 9: 300}[recon]
+                assert err <= bound, (parity, err)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("n", [1, 5, 16])
+def test_aop_and_fused_dot(prec, n):
+    """Row a3: A p = m^2 p - D_eo D_oe p with the fused <p, A p> in FP64."""
+    mass = 0.1
+    with gpu(DIMS, prec, 18) as g:
+        v = _rhs(g.lat, n, 7)
+        vin, vout = g.pack(v), g.bundle(n)
+        pap = np.zeros(n)
+        g.hisq.hisq_aop(g.fat, g.naik, mass, vin, vout, n, pap)
+        want = g.oracle.aop(v, mass)
+        assert rel_err(g.unpack(vout, n), want) <= 2 * PREC_TOL[prec]
+        vq = g.unpack(vin, n)  # the input as stored
+        want_dot = np.array([np.vdot(vq[k], g.oracle.aop(vq[k], mass)).real for k in range(n)])
+        assert np.max(np.abs(pap - want_dot) / np.abs(want_dot)) <= 4 * PREC_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_size_dslash_32c8(prec):
+    """The 32^3 x 8 lattice the benchmark runs, whole output against the oracle, n = 1 and 4."""
+    dims = (32, 32, 32, 8)
+    with gpu(dims, prec, 18) as g:
+        for n in (1, 4):
+            v = _rhs(g.lat, n, 500)
+            vin, vout = g.pack(v), g.bundle(n)
+            g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 0)
+            assert rel_err(g.unpack(vout, n), g.oracle.dslash_eo(v, 0)) <= PREC_TOL[prec]

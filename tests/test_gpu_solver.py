@@ -1,0 +1,127 @@
+"""CG solves (rows a4-a6) on the GPU through the C ABI; every solution is judged by the FP64
+oracle's true residual |b - A x| / |b|."""
+import numpy as np
+import pytest
+
+import hisq_inputs as hi
+from gpu_util import gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+SLACK = 1.01   # the library checks the same FP64 residual; allow rounding-order differences
+
+
+def _solve(g, rhs, mass, **params):
+    p = g.hisq.hisq_default_solver_params()
+    for k, v in params.items():
+        setattr(p, k, v)
+    g.hisq.hisq_set_solver_params(p)
+    xs = [np.zeros_like(b) for b in rhs]
+    g.hisq.hisq_cg_solve(g.fat, g.naik, list(rhs), xs, mass, TOL)
+    iters = np.zeros(len(rhs), dtype=np.int32)
+    res = np.zeros(len(rhs))
+    stats = g.hisq.hisq_last_stats(iters, res)
+    return np.stack(xs), stats, iters, res
+
+
+def test_config0_plain_fp64():
+    """8^3 x 4, one RHS, FP64 everywhere, m = 0.1, to true residual 1e-10; iteration count of
+    the textbook oracle CG within a few."""
+    dims = (8, 8, 8, 4)
+    with gpu(dims, 0) as g:
+        b = hi.gaussian_rhs(g.lat, 0)
+        for graph in (0, 1):
+            x, stats, iters, res = _solve(g, [b], 0.1, inner_prec=0, use_graph=graph)
+            true = g.oracle.true_residual(b, x[0], 0.1)[0]
+            assert true <= TOL * SLACK and res[0] <= TOL
+            _, it_oracle, _ = g.oracle.cg(b, 0.1, TOL)
+            assert abs(int(iters[0]) - it_oracle) <= 2
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_mixed_precision_reaches_fp64_residual(prec, graph):
+    dims = (8, 10, 8, 6)
+    with gpu(dims, prec) as g:
+        rhs = [hi.gaussian_rhs(g.lat, k) for k in range(3)]
+        x, stats, iters, res = _solve(g, rhs, 0.05, inner_prec=prec, use_graph=graph)
+        true = g.oracle.true_residual(np.stack(rhs), x, 0.05)
+        assert np.all(true <= TOL * SLACK), true
+        assert stats.converged == 3 and stats.reliable_updates >= 3
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_bundle_uneven_convergence_masked(graph):
+    """A bundle whose right-hand sides converge at different iterations (scaled norms 1e-3..1e3
+    and spectral shaping b = A^q g): converged ones are masked while the rest iterate."""
+    dims = (8, 10, 8, 6)
+    mass = 0.05
+    with gpu(dims, 1) as g:
+        rhs = []
+        for k in range(6):
+            v = hi.gaussian_rhs(g.lat, 10 + k)
+            for _ in range(k % 3):
+                v = g.oracle.aop(v, mass)
+            rhs.append(v / np.linalg.norm(v) * 10.0 ** (-3 + 6 * k / 5))
+        x, stats, iters, res = _solve(g, rhs, mass, inner_prec=1, use_graph=graph, bundle=6)
+        true = g.oracle.true_residual(np.stack(rhs), x, mass)
+        assert np.all(true <= TOL * SLACK), true
+        assert len(set(iters.tolist())) > 1
+        assert stats.bundle_iterations == max(iters)
+
+
+def test_many_rhs_in_several_bundles_and_zero_rhs():
+    dims = (8, 8, 8, 4)
+    with gpu(dims, 1) as g:
+        rhs = [hi.gaussian_rhs(g.lat, 30 + k) for k in range(19)]
+        rhs[5] = np.zeros_like(rhs[5])
+        x, stats, iters, res = _solve(g, rhs, 0.1, inner_prec=1, bundle=8)
+        assert stats.bundles == 3
+        assert np.all(x[5] == 0) and iters[5] == 0
+        ok = [k for k in range(19) if k != 5]
+        true = g.oracle.true_residual(np.stack(rhs)[ok], x[ok], 0.1)
+        assert np.all(true <= TOL * SLACK)
+
+
+def test_not_converged_is_reported():
+    dims = (8, 8, 8, 4)
+    with gpu(dims, 1) as g:
+        b = hi.gaussian_rhs(g.lat, 0)
+        p = g.hisq.hisq_default_solver_params()
+        p.max_iter = 5
+        g.hisq.hisq_set_solver_params(p)
+        x = np.zeros_like(b)
+        rc = g.hisq.hisq_cg_solve(g.fat, g.naik, [b], [x], 0.1, TOL, raise_on_error=False)
+        assert rc == -4
+        stats = g.hisq.hisq_last_stats()
+        assert stats.converged == 0 and stats.max_iterations == 5
+
+
+def test_nan_rhs_is_breakdown():
+    dims = (8, 8, 8, 4)
+    with gpu(dims, 1) as g:
+        b = hi.gaussian_rhs(g.lat, 0)
+        b[3, 1] = np.nan
+        x = np.zeros_like(b)
+        rc = g.hisq.hisq_cg_solve(g.fat, g.naik, [b], [x], 0.1, TOL, raise_on_error=False)
+        assert rc == -5
+
+
+def test_device_pointers_and_timing():
+    """rhs/x as device tensors; per-Dslash CUDA-event timing in host-driven mode."""
+    import torch
+    dims = (8, 10, 8, 6)
+    with gpu(dims, 1) as g:
+        b = hi.gaussian_rhs(g.lat, 3)
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        xd = torch.zeros_like(bd)
+        p = g.hisq.hisq_default_solver_params()
+        p.use_graph = 0
+        p.time_kernels = 1
+        g.hisq.hisq_set_solver_params(p)
+        g.hisq.hisq_cg_solve(g.fat, g.naik, [bd], [xd], 0.05, TOL)
+        stats = g.hisq.hisq_last_stats()
+        x = xd.cpu().numpy().view(np.complex128)
+        assert g.oracle.true_residual(b, x, 0.05)[0] <= TOL * SLACK
+        assert stats.dslash_launches >= 2 * stats.max_iterations and stats.dslash_ms > 0
