@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 HISQ path: mixed-precision CG on A = m^2 - D_eo D_oe to true
+residual 1e-10, with the Dslash roofline measured live and the plain FP64 CG beside it.
+
+One step = one complete solve of the 32^3 x 8 precision-form workload (m = 0.01, one Gaussian
+right-hand side, links and vectors stored in 16-bit floats with FP32 arithmetic, FP64 reliable
+updates every 10x residual drop, FP64 true residual <= 1e-10): link reads, both Dslash halves,
+the fused BLAS-1, the FP64 residual recomputations and the per-RHS control all run inside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own right-hand side on its own GPU (independent
+replicas: no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HISQ Dslash GFlop/s & HBM GB/s; CG s/RHS to res 1e-10 vs plain FP64 CG"
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="fp16", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--dims", default="32,32,32,8")
+    ap.add_argument("--mass", type=float, default=0.01)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    dims = [int(d) for d in args.dims.split(",")]
+    return dims, {
+        "workload": f"{'x'.join(map(str, dims[:3]))}x{dims[3]} even-odd HISQ CG on m^2 - D_eo D_oe, m={args.mass}, "
+                    f"1 Gaussian RHS, {args.inner} storage / fp32 arithmetic, FP64 reliable updates (delta 0.1), "
+                    f"FP64 true residual <= 1e-10",
+        "lattice": dims, "nrhs_per_gpu": 1, "mass": args.mass, "inner_storage": args.inner,
+        "fields": "synthetic SU(3) fat links (eps 0.3, 5% noise) and Naik links, staggered phases and "
+                  "antiperiodic t folded in; seeds 1/2/3, RHS seed 1000+rank",
+        "l2": "flushed between steps (512 MiB write)",
+    }
+
+
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.5)
+        return self
+
+    def mark(self, start):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            out, _ = self.proc.communicate()
+            self.lines = [l.strip() for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+            except ValueError:
+                ts = None
+            if ts is not None and self.t0 is not None and not (self.t0 - 1.0 <= ts <= self.t1 + 1.0):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(dims, inner):
+    """dram bytes per launch of the inner Dslash from the committed ncu summary, if that summary
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != kernel_source_hash():
+        return None
+    key = f"{inner}_{'x'.join(map(str, dims))}"
+    val = rec.get("per_launch_bytes", {}).get(key)
+    return float(val) if val else None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1409_1510_gb300", "csrc")
+    for name in ("dslash_kernel.cuh", "link_codec.cuh", "hisq_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------------------------
+def make_oracle(dims):
+    import hisq_inputs as hi
+    import oracle
+    lat = hi.Lattice(dims)
+    return lat, oracle.Oracle(dims, hi.fat_links(lat), hi.naik_links(lat)), hi.gaussian_rhs(lat, 0)
+
+
+def oracle_sample(lat, o, b, mass, budget_s):
+    """Time the FP64 oracle CG, as it stands, for as many iterations as fit in budget_s."""
+    t = time.perf_counter()
+    o.cg(b, mass, TOL, max_iter=1)
+    per_iter = time.perf_counter() - t
+    iters = max(1, min(500, int(budget_s / max(per_iter, 1e-6))))
+    t = time.perf_counter()
+    o.cg(b, mass, TOL, max_iter=iters)
+    el = time.perf_counter() - t
+    flops = (2 * 1146 + 72) * lat.half_volume * iters
+    return flops / el / 1e9, iters, el
+
+
+def cpu_baseline(dims, mass, budget_s=15.0):
+    """The FP64 oracle CG on a bounded sample of the same solve (single-threaded C)."""
+    lat, o, b = make_oracle(dims)
+    value, iters, el = oracle_sample(lat, o, b, mass, budget_s)
+    return {"value": value, "unit": "GFlop/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} iterations of the FP64 oracle CG on the same {dims} problem "
+                      f"({el:.1f} s, {el / iters * 1e3:.0f} ms/iteration, single-threaded C)"}
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle on this workload's config, metric and unit."""
+    dims, cfg = workload(args)
+    if rank != 0:
+        return
+    lat, o, b = make_oracle(dims)
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(lat, o, b, args.mass, 0.0)
+    per_step = 60.0 / max(1, args.steps)
+    vals, its, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        v, i, el = oracle_sample(lat, o, b, args.mass, per_step)
+        vals.append(v)
+        its += i
+        secs += el
+    value = its * (2 * 1146 + 72) * lat.half_volume / secs / 1e9
+    sample = (f"{its} FP64 oracle CG iterations on the {dims} problem over {args.steps} steps "
+              f"({secs:.1f} s, single-threaded C); one bounded sample per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "GFlop/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import accounting as acc
+    from paper_1409_1510_gb300 import hisq
+
+    dims, cfg = workload(args)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+
+    def d64(a):
+        return torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+
+    hisq.hisq_init(dims, local_rank, stream)
+    inner = PREC[args.inner]
+    fat = hisq.hisq_links_create(d64(X), False, inner, 18)
+    naik = hisq.hisq_links_create(d64(N), True, inner, 18)
+    b = d64(hi.gaussian_rhs(lat, rank))
+    x = torch.zeros_like(b)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    def set_params(prec, graph, timing=0):
+        p = hisq.hisq_default_solver_params()
+        p.inner_prec, p.use_graph, p.time_kernels, p.delta = prec, graph, timing, 0.1
+        hisq.hisq_set_solver_params(p)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(k, prec, graph, timing=0, host=False):
+        """k solves; returns (per-step ms, stats list)."""
+        set_params(prec, graph, timing)
+        ms, stats = [], []
+        if host:
+            bh = torch.empty(b.shape, dtype=torch.float64).pin_memory()
+            bh.copy_(b.cpu())
+            xh = torch.empty_like(bh).pin_memory()
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if host:
+                t = time.perf_counter()
+                hisq.hisq_cg_solve(fat, naik, [bh], [xh], args.mass, TOL)
+                ms.append((time.perf_counter() - t) * 1e3)
+            else:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hisq.hisq_cg_solve(fat, naik, [b], [x], args.mass, TOL)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            stats.append(hisq.hisq_last_stats())
+        return ms, stats
+
+    # warm-up (also autotunes and captures the solve graph)
+    timed(args.warmup, inner, 1)
+    timed(1, inner, 0, 1)
+    timed(1, 0, 1)
+
+    # ---- the timed region: K mixed-precision solves (graph mode) ----
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        clk.mark(True)
+        t_wall = time.perf_counter()
+        ms, stats = timed(args.steps, inner, 1)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        clk.mark(False)
+    total_ms = sum(ms)
+    flops = sum(s.flops for s in stats)
+    launches = sum(s.kernel_launches for s in stats)
+    iters = stats[-1].max_iterations
+    res = np.zeros(1)
+    hisq.hisq_last_stats(None, res)
+    if dist is not None:
+        t = torch.tensor([total_ms, flops, launches], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, flops_all, launches_all = float(tmax[0]), float(t[1]), float(t[2])
+    else:
+        total_ms_max, flops_all, launches_all = total_ms, flops, launches
+    value = flops_all / (total_ms_max / 1e3) / 1e9
+
+    # ---- roofline of the inner Dslash: host-driven solves with CUDA events on every launch ----
+    kr = max(3, min(args.steps, 10))
+    _, rstats = timed(kr, inner, 0, 1)
+    d_ms = sum(s.dslash_ms for s in rstats)
+    d_n = sum(s.dslash_launches for s in rstats)
+    d64_ms = sum(s.dslash64_ms for s in rstats)
+    d64_n = sum(s.dslash64_launches for s in rstats)
+    host_ms = statistics.median(s.seconds for s in rstats) * 1e3
+    elem = {0: 8, 1: 4, 2: 2, 3: 2}[inner]
+    fat_scale = 8.0 if inner in (2, 3) else 0.0       # per-site float scale of fat and Naik
+    vec_scale = 4.0 if inner == 2 else 0.0            # FP16 per-(site, RHS) scale
+    # half the launches are D_oe p (read p, write t), half m^2 p - D_eo t (also read p)
+    link_b = acc.link_bytes_per_site(elem, 18, fat_scale)
+    vec_b = acc.VECTOR_REALS * elem + vec_scale
+    bytes_per_launch = (link_b + 2.5 * vec_b) * lat.half_volume
+    avg_s = d_ms / max(d_n, 1) / 1e3
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_per_launch / avg_s / 1e9
+    traffic = kernel_traffic(dims, args.inner)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "kernel": f"dslash_kernel<{args.inner}, naik 18> inside the solve ({d_n} launches timed)",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+    dslash_gflops = acc.DSLASH_FLOPS_PER_SITE * lat.half_volume / avg_s / 1e9
+    # the FP64 residual Dslash on its own (FP64 arithmetic bound): n = 1, CUDA events, L2 flushed
+    fat64 = hisq.hisq_links_create(d64(X), False, 0, 18)
+    naik64 = hisq.hisq_links_create(d64(N), True, 0, 18)
+    v64 = torch.empty(hisq.hisq_vector_bytes(0, 1), dtype=torch.uint8, device=dev)
+    hisq.hisq_pack(b, v64, 1, 0)
+    w64 = torch.empty_like(v64)
+    hisq.hisq_dslash(fat64, naik64, v64, w64, 1, 1)
+    t64 = []
+    for i in range(10):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hisq.hisq_dslash(fat64, naik64, v64, w64, 1, i % 2)
+        e1.record(stream)
+        e1.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    hisq.hisq_links_destroy(fat64)
+    hisq.hisq_links_destroy(naik64)
+    fp64_dslash_gflops = acc.DSLASH_FLOPS_PER_SITE * lat.half_volume / (statistics.median(t64) / 1e3) / 1e9
+
+    # ---- plain FP64 CG (the comparator) and the other inner precisions ----
+    k64 = max(3, min(args.steps, 10))
+    ms64, st64 = timed(k64, 0, 1)
+    fp64_s = statistics.median(ms64) / 1e3
+    variants = {}
+    for name in ("fp32", "fp16", "bf16"):
+        if name == args.inner:
+            continue
+        fv = hisq.hisq_links_create(d64(X), False, PREC[name], 18)
+        nv = hisq.hisq_links_create(d64(N), True, PREC[name], 18)
+        fat_s, naik_s = fat, naik
+        fat, naik = fv, nv
+        timed(2, PREC[name], 1)
+        vms, vst = timed(k64, PREC[name], 1)
+        variants[name] = {"s_per_rhs": statistics.median(vms) / 1e3, "iterations": vst[-1].max_iterations}
+        fat, naik = fat_s, naik_s
+        hisq.hisq_links_destroy(fv)
+        hisq.hisq_links_destroy(nv)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    ke = max(3, min(args.steps, 20))
+    ems, est = timed(ke, inner, 1, host=True)
+    e2e_value = sum(s.flops for s in est) / (sum(ems) / 1e3) / 1e9
+    vbytes = lat.half_volume * 6 * 8
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(dims, args.mass)
+        s_rhs = total_ms / 1e3 / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+            "cg_s_per_rhs": s_rhs, "fp64_cg_s_per_rhs": fp64_s, "speedup_vs_fp64_cg": fp64_s / s_rhs,
+            "iterations": iters, "reliable_updates": stats[-1].reliable_updates, "true_residual": float(res[0]),
+            "fp64_cg_iterations": st64[-1].max_iterations,
+            "dslash": {"gflops": dslash_gflops, "hbm_gbs": achieved, "precision": args.inner,
+                       "fp64_residual_dslash_gflops": fp64_dslash_gflops, "nrhs": 1},
+            "host_driven_ms_per_step": host_ms, "other_inner_precisions": variants,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GFlop/s", "h2d_bytes_per_step": vbytes, "d2h_bytes_per_step": vbytes},
+            "gpu_launches": int(launches_all), "clocks": clk.summary(), "wall_s_timed_region": t_wall,
+        }
+    hisq.hisq_finalize()
+    return line
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist = tdist
+    line = run_ours(args, rank, world, local_rank, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

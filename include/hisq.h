@@ -168,9 +168,13 @@ typedef struct {
     int reliable_updates;     /* FP64 residual recomputations, summed over right-hand sides */
     int fallbacks;            /* flexible-CG stalls that switched to plain CG */
     double seconds;           /* wall time of the hisq_cg_solve call */
-    double dslash_ms;         /* summed Dslash kernel time (time_kernels = 1 only) */
-    int dslash_launches;      /* Dslash launches timed */
+    double dslash_ms;         /* summed inner-precision Dslash kernel time (time_kernels = 1,
+                                 host-driven mode only) */
+    int dslash_launches;      /* inner-precision Dslash launches timed */
+    double dslash64_ms;       /* summed FP64 (residual recomputation) Dslash kernel time */
+    int dslash64_launches;
     double flops;             /* useful flops: (2*1146 + 72) per even site, RHS and iteration */
+    long kernel_launches;     /* kernels of this library launched by the solve */
 } hisq_solve_stats;
 
 /* Statistics of the calling thread's last hisq_cg_solve.  iterations (int[nrhs]) and
@@ -206,10 +210,12 @@ int hisq_pc_get_weights(const hisq_pc *pc, double *weights /* host */);
 int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
                   const void *in, void *out, int nrhs);
 
-/* Training loss (1/K) sum_k |M r_k - e_k|^2 / |e_k|^2 over K pairs and its gradient
- * dL/dRe W + i dL/dIm W (host double[HISQ_PC_WEIGHTS][2]); r, e: device FP32 internal bundles
- * of K (1..HISQ_MAX_BUNDLE) vectors each. */
-int hisq_pc_loss_grad(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+/* Training loss over K pairs (r_k, e_k) with A e_k = r_k (residual and error of a CG iterate):
+ *   loss = (1/K) sum_k |A (M r_k - e_k)|^2 / |r_k|^2,  A = mass^2 - D_eo D_oe,
+ * i.e. the error of the network's correction measured in the residual norm, and its gradient
+ * dL/dRe W + i dL/dIm W (host or device double[HISQ_PC_WEIGHTS][2]); r, e: device FP32 internal
+ * bundles of K (1..HISQ_MAX_BUNDLE) vectors each. */
+int hisq_pc_loss_grad(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
                       const void *r, const void *e, int K, double *loss, double *grad);
 
 /* One Adam step (Kingma & Ba) on the real and imaginary parts of the weights, on the GPU:
@@ -219,10 +225,11 @@ int hisq_pc_adam_step(hisq_pc *pc, const double *grad, int step, double lr, doub
 
 /* Train on K pairs (device FP32 internal, stored as ceil(K/16) consecutive bundles of 16
  * vectors, the last one padded) for `epochs` passes of minibatches of `batch` (<= 16) pairs
- * with Adam at learning rate lr.  loss_history (host, epochs doubles, may be NULL) receives
- * the mean loss of each epoch. */
-int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *r,
-                  const void *e, int K, int batch, int epochs, double lr, double *loss_history);
+ * with Adam at learning rate lr, on the loss of hisq_pc_loss_grad.  loss_history (host, epochs
+ * doubles, may be NULL) receives the mean loss of each epoch. */
+int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
+                  const void *r, const void *e, int K, int batch, int epochs, double lr,
+                  double *loss_history);
 
 #ifdef __cplusplus
 }

@@ -38,10 +38,11 @@ def _bind(so):
     so.oracle_pc_layer.argtypes = [_I4, _D, _D, ctypes.c_int, ctypes.c_int, _D, _D, _D]
     so.oracle_pc_num_weights.restype = ctypes.c_long
     so.oracle_pc_forward.argtypes = [_I4, _D, _D, _D, _D, _D]
-    so.oracle_pc_loss_grad.argtypes = [_I4, _D, _D, _D, ctypes.c_int, _D, _D, _D]
+    so.oracle_pc_loss_grad.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, _D]
     so.oracle_pc_loss_grad.restype = ctypes.c_double
     so.oracle_adam_step.argtypes = [ctypes.c_long, _D, _D, _D, _D, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    so.oracle_pc_backward.argtypes = [_I4, _D, _D, _D, _D, _D, _D]
     so.oracle_fcg.argtypes = [_I4, _D, _D, ctypes.c_double, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
     so.oracle_fcg.restype = ctypes.c_int
     return so
@@ -130,15 +131,25 @@ class Oracle:
         self._so.oracle_pc_forward(self._L, _p(self.X), _p(self.N), _p(W), _p(r), _p(y))
         return y
 
-    def pc_loss_grad(self, W, r, e, with_grad: bool = True):
-        """(loss, grad) over K pairs r, e [K][V/2][3]; grad = dL/dReW + i dL/dImW."""
+    def pc_loss_grad(self, W, r, e, mass: float, with_grad: bool = True):
+        """(loss, grad) over K pairs r, e [K][V/2][3] with A e = r:
+        loss = mean_k |A (M r_k - e_k)|^2 / |r_k|^2; grad = dL/dReW + i dL/dImW."""
         W = _c(W).reshape(-1)
         r = _c(r).reshape(-1, self.V // 2, 3)
         e = _c(e).reshape(-1, self.V // 2, 3)
         g = np.zeros_like(W)
-        loss = self._so.oracle_pc_loss_grad(self._L, _p(self.X), _p(self.N), _p(W), r.shape[0],
+        loss = self._so.oracle_pc_loss_grad(self._L, _p(self.X), _p(self.N), float(mass), _p(W), r.shape[0],
                                             _p(r), _p(e), _p(g) if with_grad else None)
         return loss, g
+
+    def pc_backward(self, W, r, gy):
+        """Weight gradient (layout of W) for one input r given dL/dRe y + i dL/dIm y on even sites."""
+        W = _c(W).reshape(-1)
+        r = _c(r).reshape(self.V // 2, 3)
+        gy = _c(gy).reshape(self.V // 2, 3)
+        g = np.zeros_like(W)
+        self._so.oracle_pc_backward(self._L, _p(self.X), _p(self.N), _p(W), _p(r), _p(gy), _p(g))
+        return g
 
     def fcg(self, W, b, mass: float, tol: float = 1e-10, max_iter: int = 10000):
         """Flexible CG with the network as preconditioner; returns (x, iterations, true rel)."""

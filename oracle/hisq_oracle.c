@@ -352,52 +352,63 @@ static void layer_backward(const int L[4], const double *X, const double *N, int
 }
 
 /*
- * Training loss and gradient over K pairs (r_k, e_k), each [V/2][3][2]:
- *   loss = (1/K) sum_k |M r_k - e_k|^2 / |e_k|^2.
- * grad receives dloss/dRe W + i dloss/dIm W for every complex weight (same layout as W).
+ * Weight gradient of a real loss through the network for one input r [V/2][3][2], given the
+ * loss gradient with respect to the network output, gy = dL/dRe y + i dL/dIm y on the even sites
+ * [V/2][3][2].  Accumulates into grad (layout of W) the chain rule of oracle_pc_loss_grad.
  */
-double oracle_pc_loss_grad(const int L[4], const double *X, const double *N, const double *W,
-                           int K, const double *r, const double *e, double *grad) {
-    long V = volume(L), Vh = V / 2, n = V * 3;
-    long nw = oracle_pc_num_weights();
-    double *h0 = (double *)malloc(sizeof(double) * n * 2);
+void oracle_pc_backward(const int L[4], const double *X, const double *N, const double *W,
+                        const double *r, const double *gy, double *grad) {
+    long V = volume(L), n = V * 3;
+    double *h0 = (double *)calloc((size_t)n * 2, sizeof(double));
     double *h1 = (double *)malloc(sizeof(double) * n * 2 * 4);
     double *h2 = (double *)malloc(sizeof(double) * n * 2 * 4);
-    double *h3 = (double *)malloc(sizeof(double) * n * 2);
-    double *g3 = (double *)malloc(sizeof(double) * n * 2);
+    double *g3 = (double *)calloc((size_t)n * 2, sizeof(double));
     double *g2 = (double *)malloc(sizeof(double) * n * 2 * 4);
     double *g1 = (double *)malloc(sizeof(double) * n * 2 * 4);
+    for (long x = 0; x < V; x++)
+        if (parity_of(L, x) == 0)
+            for (int a = 0; a < 3; a++) {
+                put(h0, x, a, vec(r, x / 2, a));
+                put(g3, x, a, vec(gy, x / 2, a));
+            }
+    oracle_pc_layer(L, X, N, 1, 4, layer_weights(W, 0), h0, h1);
+    oracle_pc_layer(L, X, N, 4, 4, layer_weights(W, 1), h1, h2);
+    layer_backward(L, X, N, 4, 1, layer_weights(W, 2), h2, g3, grad + (layer_weights(W, 2) - W), g2);
+    layer_backward(L, X, N, 4, 4, layer_weights(W, 1), h1, g2, grad + (layer_weights(W, 1) - W), g1);
+    layer_backward(L, X, N, 1, 4, layer_weights(W, 0), h0, g1, grad + (layer_weights(W, 0) - W), NULL);
+    free(h0); free(h1); free(h2); free(g3); free(g2); free(g1);
+}
+
+/*
+ * Training loss and gradient over K pairs (r_k, e_k), each [V/2][3][2] with A e_k = r_k: the
+ * error of the network's correction measured in the residual norm,
+ *   loss = (1/K) sum_k |A (M r_k - e_k)|^2 / |r_k|^2,
+ * so that lambda p(lambda) ~ 1 is fitted over the whole spectrum of A (what CG needs).
+ * grad receives dloss/dRe W + i dloss/dIm W for every complex weight (same layout as W).
+ * The output gradient is gy_k = 2 A (A (y_k - e_k)) / (K |r_k|^2) (A is Hermitian).
+ */
+double oracle_pc_loss_grad(const int L[4], const double *X, const double *N, double mass, const double *W,
+                           int K, const double *r, const double *e, double *grad) {
+    long Vh = volume(L) / 2, m = Vh * 3;
+    long nw = oracle_pc_num_weights();
+    double *y = (double *)malloc(sizeof(double) * m * 2);
+    double *d = (double *)malloc(sizeof(double) * m * 2);
+    double *gy = (double *)malloc(sizeof(double) * m * 2);
     double loss = 0.0;
     if (grad) memset(grad, 0, sizeof(double) * nw * 2);
     for (int k = 0; k < K; k++) {
         const double *rk = r + (long)k * Vh * 6, *ek = e + (long)k * Vh * 6;
-        memset(h0, 0, sizeof(double) * n * 2);
-        for (long x = 0; x < V; x++)
-            if (parity_of(L, x) == 0)
-                for (int a = 0; a < 3; a++) put(h0, x, a, vec(rk, x / 2, a));
-        oracle_pc_layer(L, X, N, 1, 4, layer_weights(W, 0), h0, h1);
-        oracle_pc_layer(L, X, N, 4, 4, layer_weights(W, 1), h1, h2);
-        oracle_pc_layer(L, X, N, 4, 1, layer_weights(W, 2), h2, h3);
-        double enorm2 = norm2(ek, Vh * 3), err2 = 0.0;
-        memset(g3, 0, sizeof(double) * n * 2);
-        for (long x = 0; x < V; x++) {
-            if (parity_of(L, x) != 0) continue;
-            for (int a = 0; a < 3; a++) {
-                cplx d = c_sub(vec(h3, x, a), vec(ek, x / 2, a));
-                err2 += d.re * d.re + d.im * d.im;
-                put(g3, x, a, c_scale(2.0 / (K * enorm2), d));
-            }
-        }
-        loss += err2 / enorm2 / K;
+        oracle_pc_forward(L, X, N, W, rk, y);
+        for (long i = 0; i < 2 * m; i++) y[i] -= ek[i];
+        oracle_aop(L, X, N, mass, y, d, 1);                 /* d = A (y - e) */
+        double rnorm2 = norm2(rk, m);
+        loss += norm2(d, m) / rnorm2 / K;
         if (!grad) continue;
-        double *gw3 = grad + (layer_weights(W, 2) - W);
-        double *gw2 = grad + (layer_weights(W, 1) - W);
-        double *gw1 = grad + (layer_weights(W, 0) - W);
-        layer_backward(L, X, N, 4, 1, layer_weights(W, 2), h2, g3, gw3, g2);
-        layer_backward(L, X, N, 4, 4, layer_weights(W, 1), h1, g2, gw2, g1);
-        layer_backward(L, X, N, 1, 4, layer_weights(W, 0), h0, g1, gw1, NULL);
+        oracle_aop(L, X, N, mass, d, gy, 1);                /* gy = A d */
+        for (long i = 0; i < 2 * m; i++) gy[i] *= 2.0 / (K * rnorm2);
+        oracle_pc_backward(L, X, N, W, rk, gy, grad);
     }
-    free(h0); free(h1); free(h2); free(h3); free(g3); free(g2); free(g1);
+    free(y); free(d); free(gy);
     return loss;
 }
 

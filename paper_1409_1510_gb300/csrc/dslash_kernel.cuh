@@ -70,14 +70,16 @@ __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int n
         }
         __syncthreads();
         for (int j = tid; j < ndots; j += blockDim.x) ra.partials[(size_t)blockIdx.x * ndots + j] = red[j];
+        // only the threads that published partials fence them before the ticket is taken
+        if (tid < ndots) __threadfence();
     }
-    __threadfence();
     __shared__ int is_last;
     __syncthreads();
     if (tid == 0) is_last = (atomicAdd(ra.counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!is_last) return;
-    __threadfence();
+    if (tid == 0) __threadfence();
+    __syncthreads();
     if (ndots > 0) {
         int nchunks = 1;
         while (nchunks * 2 * ndots <= (int)blockDim.x) nchunks *= 2;

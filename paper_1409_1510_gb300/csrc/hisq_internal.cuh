@@ -307,6 +307,9 @@ LaunchShape default_shape(int prec, int n);
 LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64);
 void free_workspace(hisq_ctx *ctx);  // solver.cu
 void free_pc(hisq_pc *pc);           // pc.cu
+int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
+               void *out, int n, cudaStream_t st);
+int pc_prepare(hisq_ctx *ctx, const hisq_pc *pc, int n);  // allocate the network workspace
 int pack_vectors(hisq_ctx *ctx, const double *canon_dev, void *internal, int n, int prec, cudaStream_t st);
 int unpack_vectors(hisq_ctx *ctx, const void *internal, double *canon_dev, int n, int prec, cudaStream_t st);
 }  // namespace hisq

@@ -8,36 +8,30 @@
 
 namespace hisq {
 
-// ---- training loss: G3 = 2 (y - e) / (K |e|^2) on even sites, per-sample |y - e|^2 ----------
+// ---- training loss pieces --------------------------------------------------------------------
 struct LossArgs {
     int Vh, K, spb;
     const float2 *y, *e;
-    const double *e2;   // [K] |e_k|^2
+    const double *e2;   // [K] |r_k|^2
     float2 *G;          // [Vh][3][K]
     RedArgs red;
 };
 
-__global__ void __launch_bounds__(256) pc_loss_kernel(LossArgs a) {
-    extern __shared__ double red[];
-    const int k = threadIdx.x % a.K, sl = threadIdx.x / a.K;
-    const int rows = blockDim.x / a.K;
-    double acc = 0.0;
-    const float scale = (float)(2.0 / ((double)a.K * a.e2[k]));
-    for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
-        int s = tile * a.spb + sl;
-        if (s >= a.Vh || sl >= a.spb) continue;
-        for (int c = 0; c < 3; c++) {
-            size_t i = ((size_t)s * 3 + c) * a.K + k;
-            float2 y = a.y[i], e = a.e[i];
-            float dr = y.x - e.x, di = y.y - e.y;
-            acc += (double)(dr * dr + di * di);
-            a.G[i] = make_float2(scale * dr, scale * di);
-        }
+// u = y - e
+__global__ void pc_sub_kernel(long n, const float2 *y, const float2 *e, float2 *u) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float2 a = y[i], b = e[i];
+        u[i] = make_float2(a.x - b.x, a.y - b.y);
     }
-    for (int i = threadIdx.x; i < rows * a.K; i += blockDim.x) red[i] = 0.0;
-    __syncthreads();
-    if (sl < rows) red[sl * a.K + k] = acc;
-    block_reduce_finish(red, rows, a.K, 0, a.red);
+}
+
+// G *= 2 / (K |r_k|^2) for sample k = i % K
+__global__ void pc_scale_kernel(long n, int K, const double *r2, float2 *G) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float s = (float)(2.0 / ((double)K * r2[i % K]));
+        float2 g = G[i];
+        G[i] = make_float2(s * g.x, s * g.y);
+    }
 }
 
 // per-sample |v_k|^2 of a [Vh][3][K] FP32 field
@@ -101,6 +95,9 @@ struct PcWork {
     float2 *h1[2] = {nullptr, nullptr}, *h2[2] = {nullptr, nullptr};  // 4 channels per parity
     float2 *g1[2] = {nullptr, nullptr}, *g2[2] = {nullptr, nullptr};
     float2 *y = nullptr, *G3 = nullptr;   // 1 channel, even
+    float2 *u = nullptr, *d = nullptr;    // 1 channel, even: y - e and A (y - e)
+    float2 *t = nullptr;                  // 1 channel, odd: intermediate of A
+    double *r2 = nullptr, *dots = nullptr;
     double *gbuf = nullptr;               // [3 layers][2 parity][17*16*2]
     double *e2 = nullptr, *err2 = nullptr, *grad = nullptr;
     double *partials = nullptr;
@@ -122,7 +119,7 @@ static void free_work(PcWork &w) {
         if (w.g2[p]) cudaFree(w.g2[p]);
         w.h1[p] = w.h2[p] = w.g1[p] = w.g2[p] = nullptr;
     }
-    void *bufs[] = {w.y, w.G3, w.gbuf, w.e2, w.err2, w.grad, w.partials, w.counter};
+    void *bufs[] = {w.y, w.G3, w.u, w.d, w.t, w.r2, w.dots, w.gbuf, w.e2, w.err2, w.grad, w.partials, w.counter};
     for (void *b : bufs)
         if (b) cudaFree(b);
     w = PcWork();
@@ -140,6 +137,9 @@ static int ensure_work(hisq_ctx *ctx, hisq_pc *pc, int K) {
         ok = ok && cudaMalloc(&w.h1[p], f4) == cudaSuccess && cudaMalloc(&w.h2[p], f4) == cudaSuccess &&
              cudaMalloc(&w.g1[p], f4) == cudaSuccess && cudaMalloc(&w.g2[p], f4) == cudaSuccess;
     ok = ok && cudaMalloc(&w.y, f1) == cudaSuccess && cudaMalloc(&w.G3, f1) == cudaSuccess &&
+         cudaMalloc(&w.u, f1) == cudaSuccess && cudaMalloc(&w.d, f1) == cudaSuccess &&
+         cudaMalloc(&w.t, f1) == cudaSuccess && cudaMalloc(&w.r2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
+         cudaMalloc(&w.dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) == cudaSuccess &&
          cudaMalloc(&w.gbuf, sizeof(double) * 3 * 2 * PC_PATHS * 16 * 2) == cudaSuccess &&
          cudaMalloc(&w.e2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
          cudaMalloc(&w.err2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
@@ -157,6 +157,12 @@ static int ensure_work(hisq_ctx *ctx, hisq_pc *pc, int K) {
 }
 
 // ---- launches -------------------------------------------------------------------------------
+static int pow2_floor_pc(int x) {
+    int p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
+
 static PcLayerArgs layer_args(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int K, int parity) {
     PcLayerArgs p;
     memset(&p, 0, sizeof(p));
@@ -164,7 +170,7 @@ static PcLayerArgs layer_args(hisq_ctx *ctx, const hisq_links *fat, const hisq_l
     p.fat = fat->field();
     p.naik = naik->field();
     p.K = K;
-    p.spb = 256 / K;
+    p.spb = pow2_floor_pc(256 / K);  // kernels run 256 threads; threads with sl >= spb idle
     p.parity = parity;
     return p;
 }
@@ -317,7 +323,7 @@ static int backward(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const his
 }
 
 static int reduce_launch(hisq_ctx *ctx, void (*k)(LossArgs), LossArgs a, cudaStream_t st) {
-    int threads = 256;
+    int threads = a.spb * a.K;  // rows of the block reduction (spb) must be a power of two
     size_t smem = threads * sizeof(double);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
@@ -328,23 +334,53 @@ static int reduce_launch(hisq_ctx *ctx, void (*k)(LossArgs), LossArgs a, cudaStr
     return HISQ_OK;
 }
 
-static int loss_and_grad(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const float2 *r,
-                         const float2 *e, int K, cudaStream_t st) {
+// out = A in = m^2 in - D_eo D_oe in for K FP32 even-site vectors (t: odd intermediate)
+static int apply_a(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, PcWork &w, double mass,
+                   const float2 *in, float2 *out, int K, cudaStream_t st) {
+    DslashArgs d;
+    memset(&d, 0, sizeof(d));
+    d.in = in;
+    d.out = w.t;
+    d.n = K;
+    d.parity = 1;
+    d.epi = EPI_PLAIN;
+    HISQ_CHECK(launch_dslash(ctx, fat, naik, false, d, nullptr, st));
+    d.in = w.t;
+    d.out = out;
+    d.parity = 0;
+    d.epi = EPI_AOP;
+    d.mass2 = mass * mass;
+    d.axpy_in = in;
+    d.partials = w.partials;
+    d.partials_cap = w.partials_cap;
+    d.counter = w.counter;
+    d.dot_out = w.dots;
+    return launch_dslash(ctx, fat, naik, false, d, nullptr, st);
+}
+
+// loss = mean_k |A (M r_k - e_k)|^2 / |r_k|^2 and its weight gradient (gbuf)
+static int loss_and_grad(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
+                         const float2 *r, const float2 *e, int K, cudaStream_t st) {
     PcWork &w = pcw(pc);
+    const long n = (long)ctx->geom.Vh * 3 * K;
+    const int blocks = (int)std::min<long>((n + 255) / 256, (long)ctx->num_sms * 8);
     LossArgs a;
     memset(&a, 0, sizeof(a));
     a.Vh = ctx->geom.Vh;
     a.K = K;
-    a.spb = 256 / K;
-    a.e = e;
-    a.red = red_of(w, w.e2);
-    HISQ_CHECK(reduce_launch(ctx, pc_norm_kernel, a, st));
-    HISQ_CHECK(forward(ctx, pc, fat, naik, r, w.y, K, st));
-    a.y = w.y;
-    a.e2 = w.e2;
-    a.G = w.G3;
+    a.spb = pow2_floor_pc(256 / K);
+    a.e = r;
+    a.red = red_of(w, w.r2);
+    HISQ_CHECK(reduce_launch(ctx, pc_norm_kernel, a, st));                 // |r_k|^2
+    HISQ_CHECK(forward(ctx, pc, fat, naik, r, w.y, K, st));                 // y = M r
+    pc_sub_kernel<<<blocks, 256, 0, st>>>(n, w.y, e, w.u);                  // u = y - e
+    HISQ_CHECK(apply_a(ctx, fat, naik, w, mass, w.u, w.d, K, st));          // d = A u
+    a.e = w.d;
     a.red = red_of(w, w.err2);
-    HISQ_CHECK(reduce_launch(ctx, pc_loss_kernel, a, st));
+    HISQ_CHECK(reduce_launch(ctx, pc_norm_kernel, a, st));                 // |d_k|^2
+    HISQ_CHECK(apply_a(ctx, fat, naik, w, mass, w.d, w.G3, K, st));         // G3 = A d
+    pc_scale_kernel<<<blocks, 256, 0, st>>>(n, K, w.r2, w.G3);              // G3 *= 2 / (K |r|^2)
+    HISQ_CUDA(cudaGetLastError());
     return backward(ctx, pc, fat, naik, r, K, st);
 }
 
@@ -378,6 +414,8 @@ void free_pc(hisq_pc *pc) {
     if (pc->d_v) cudaFree(pc->d_v);
     delete pc;
 }
+
+int pc_prepare(hisq_ctx *ctx, const hisq_pc *pc, int n) { return ensure_work(ctx, const_cast<hisq_pc *>(pc), n); }
 
 int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
                void *out, int n, cudaStream_t st) {
@@ -468,8 +506,8 @@ int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *na
     return pc_forward(ctx, pc, fat, naik, in, out, nrhs, ctx->stream);
 }
 
-int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_links *naik, const void *r, const void *e,
-                      int K, double *loss, double *grad) {
+int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_links *naik, double mass, const void *r,
+                      const void *e, int K, double *loss, double *grad) {
     hisq_ctx *ctx;
     HISQ_CHECK(require_ctx(&ctx));
     HISQ_CHECK(check_args(ctx, pc_c, fat, naik));
@@ -479,11 +517,11 @@ int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_lin
     HISQ_CHECK(ensure_work(ctx, pc, K));
     PcWork &w = pcw(pc);
     cudaStream_t st = ctx->stream;
-    HISQ_CHECK(loss_and_grad(ctx, pc, fat, naik, reinterpret_cast<const float2 *>(r), reinterpret_cast<const float2 *>(e),
-                             K, st));
+    HISQ_CHECK(loss_and_grad(ctx, pc, fat, naik, mass, reinterpret_cast<const float2 *>(r),
+                             reinterpret_cast<const float2 *>(e), K, st));
     double err2[HISQ_MAX_BUNDLE], e2[HISQ_MAX_BUNDLE];
     HISQ_CUDA(cudaMemcpyAsync(err2, w.err2, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
-    HISQ_CUDA(cudaMemcpyAsync(e2, w.e2, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+    HISQ_CUDA(cudaMemcpyAsync(e2, w.r2, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
     if (grad) {
         pc_sum_grad_kernel<<<(2 * HISQ_PC_WEIGHTS + 255) / 256, 256, 0, st>>>(w.gbuf, w.grad);
         HISQ_CUDA(cudaMemcpyAsync(grad, w.grad, sizeof(double) * 2 * HISQ_PC_WEIGHTS, cudaMemcpyDefault, st));
@@ -517,8 +555,8 @@ int hisq_pc_adam_step(hisq_pc *pc, const double *grad, int step, double lr, doub
     return HISQ_OK;
 }
 
-int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *r, const void *e, int K,
-                  int batch, int epochs, double lr, double *loss_history) {
+int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass, const void *r, const void *e,
+                  int K, int batch, int epochs, double lr, double *loss_history) {
     hisq_ctx *ctx;
     HISQ_CHECK(require_ctx(&ctx));
     HISQ_CHECK(check_args(ctx, pc, fat, naik));
@@ -561,7 +599,7 @@ int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, co
                     rc = set_error(HISQ_ERR_CUDA, "minibatch gather failed: %s", cudaGetErrorString(ce));
                     break;
                 }
-                rc = loss_and_grad(ctx, pc, fat, naik, rb, eb, batch, st);
+                rc = loss_and_grad(ctx, pc, fat, naik, mass, rb, eb, batch, st);
                 if (rc != HISQ_OK) break;
                 step++;
                 pc_adam_kernel<<<(2 * HISQ_PC_WEIGHTS + 255) / 256, 256, 0, st>>>(pc->d_theta, pc->d_m, pc->d_v, w.gbuf,
@@ -569,7 +607,7 @@ int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, co
                                                                                   pc->d_weights);
                 double err2[HISQ_MAX_BUNDLE], e2[HISQ_MAX_BUNDLE];
                 cudaMemcpyAsync(err2, w.err2, sizeof(double) * batch, cudaMemcpyDeviceToHost, st);
-                cudaMemcpyAsync(e2, w.e2, sizeof(double) * batch, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(e2, w.r2, sizeof(double) * batch, cudaMemcpyDeviceToHost, st);
                 ce = cudaStreamSynchronize(st);
                 if (ce != cudaSuccess) {
                     rc = set_error(HISQ_ERR_CUDA, "training step failed: %s", cudaGetErrorString(ce));

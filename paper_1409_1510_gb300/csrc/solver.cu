@@ -185,6 +185,114 @@ __global__ void __launch_bounds__(256) cg_xhi_kernel(BlasArgs a) {
     }
 }
 
+// ---- flexible CG (row a9) -------------------------------------------------------------------
+// zz = z (network output) or r (after a stall fallback); dots <r - r_old, zz> -> HOOK_FCG_BETA
+template <int P>
+__global__ void __launch_bounds__(256) fcg_beta_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    using rq = typename Prec<Q>::real;
+    extern __shared__ double red[];
+    BLAS_PROLOGUE
+    auto vr = view<Q>(a.r, a.Vh, a.n);
+    auto vro = view<Q>(a.r_old, a.Vh, a.n);
+    auto vz = view<P>(a.z, a.Vh, a.n);
+    const bool act = a.st->active[r] != 0 && !a.st->restart[r];
+    const bool use_r = a.st->fallback[r] != 0;
+    double acc_re = 0.0, acc_im = 0.0;
+    if (act) {
+        for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+            int s = tile * a.spb + sl;
+            if (s >= a.Vh || sl >= a.spb) continue;
+            Cplx<rq> rv[3], ro[3];
+            Cplx<typename Prec<P>::real> z[3];
+            load3<Q>(vr, s, r, rv);
+            load3<Q>(vro, s, r, ro);
+            if (use_r) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) z[c] = {(typename Prec<P>::real)rv[c].re, (typename Prec<P>::real)rv[c].im};
+            } else {
+                load3<P>(vz, s, r, z);
+            }
+            rq pre = 0, pim = 0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {  // conj(r - r_old) z
+                rq dre = rv[c].re - ro[c].re, dim = rv[c].im - ro[c].im;
+                pre += dre * (rq)z[c].re + dim * (rq)z[c].im;
+                pim += dre * (rq)z[c].im - dim * (rq)z[c].re;
+            }
+            acc_re += (double)pre;
+            acc_im += (double)pim;
+        }
+    }
+    const int rows = blockDim.x / a.n;
+    for (int i = tid; i < rows * 2 * a.n; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (sl < rows) {
+        red[sl * 2 * a.n + 2 * r] = acc_re;
+        red[sl * 2 * a.n + 2 * r + 1] = acc_im;
+    }
+    block_reduce_finish(red, rows, 2 * a.n, a.n, a.red);
+}
+
+// p = zz + beta p (complex beta); r_old = r; dots <p, r> -> HOOK_FCG_PR
+template <int P>
+__global__ void __launch_bounds__(256) fcg_pupdate_kernel(BlasArgs a) {
+    constexpr int Q = q_prec(P);
+    using rq = typename Prec<Q>::real;
+    using rp = typename Prec<P>::real;
+    extern __shared__ double red[];
+    BLAS_PROLOGUE
+    auto vr = view<Q>(a.r, a.Vh, a.n);
+    auto vro = view<Q>(a.r_old, a.Vh, a.n);
+    auto vz = view<P>(a.z, a.Vh, a.n);
+    auto vp = view<P>(a.p, a.Vh, a.n);
+    const bool act = a.st->active[r] != 0;
+    const bool use_r = a.st->fallback[r] != 0;
+    const rp b_re = (rp)a.st->beta[r][0], b_im = (rp)a.st->beta[r][1];
+    double acc_re = 0.0, acc_im = 0.0;
+    if (act) {
+        for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+            int s = tile * a.spb + sl;
+            if (s >= a.Vh || sl >= a.spb) continue;
+            Cplx<rq> rv[3];
+            Cplx<rp> z[3], p[3];
+            load3<Q>(vr, s, r, rv);
+            load3<P>(vp, s, r, p);
+            if (use_r) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) z[c] = {(rp)rv[c].re, (rp)rv[c].im};
+            } else {
+                load3<P>(vz, s, r, z);
+            }
+            rq pre = 0, pim = 0;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                p[c] = {z[c].re + b_re * p[c].re - b_im * p[c].im, z[c].im + b_re * p[c].im + b_im * p[c].re};
+                pre += (rq)p[c].re * rv[c].re + (rq)p[c].im * rv[c].im;   // conj(p) r
+                pim += (rq)p[c].re * rv[c].im - (rq)p[c].im * rv[c].re;
+            }
+            acc_re += (double)pre;
+            acc_im += (double)pim;
+            store_site<P>(vp, s, r, p);
+            store_site<Q>(vro, s, r, rv);
+        }
+    }
+    const int rows = blockDim.x / a.n;
+    for (int i = tid; i < rows * 2 * a.n; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (sl < rows) {
+        red[sl * 2 * a.n + 2 * r] = acc_re;
+        red[sl * 2 * a.n + 2 * r + 1] = acc_im;
+    }
+    block_reduce_finish(red, rows, 2 * a.n, a.n, a.red);
+}
+
+// single block: runs the end-of-iteration hook
+__global__ void loop_hook_kernel(RedArgs ra, int n) {
+    __shared__ double red[32];
+    block_reduce_finish(red, 1, 0, n, ra);
+}
+
 // ------------------------------------------------------------------------------------------
 // Workspace
 // ------------------------------------------------------------------------------------------
@@ -304,7 +412,9 @@ struct Solve {
     double mass;
     cudaStream_t st;
     bool timing;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events;    // inner-precision Dslash
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events64;  // FP64 Dslash
+    const hisq_pc *pc;                                           // flexible CG when set
 };
 
 static BlasArgs blas_args(const Solve &S) {
@@ -335,7 +445,7 @@ static BlasArgs blas_args(const Solve &S) {
 template <typename K>
 static int launch_blas(const Solve &S, K kernel, BlasArgs a, int hook, bool reduce) {
     int threads = a.spb * a.n;
-    size_t smem = reduce ? (size_t)std::max(threads, a.spb * a.n) * sizeof(double) : 0;
+    size_t smem = reduce ? (size_t)std::max(threads, a.spb * a.n * 2) * sizeof(double) : 0;
     long tiles = (a.Vh + a.spb - 1) / a.spb;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
@@ -354,6 +464,8 @@ static int enqueue_blas(const Solve &S, int which) {
     case HOOK_INIT: return launch_blas(S, cg_init_kernel<P>, a, HOOK_INIT, true);
     case HOOK_DECIDE: return launch_blas(S, cg_update_kernel<P>, a, HOOK_DECIDE, true);
     case HOOK_LOOP: return launch_blas(S, cg_pupdate_kernel<P>, a, HOOK_LOOP, true);
+    case HOOK_FCG_BETA: return launch_blas(S, fcg_beta_kernel<P>, a, HOOK_FCG_BETA, true);
+    case HOOK_FCG_PR: return launch_blas(S, fcg_pupdate_kernel<P>, a, HOOK_FCG_PR, true);
     default: {
         a.gate = &S.w->st->any_update;
         return launch_blas(S, cg_xhi_kernel<P>, a, HOOK_NONE, false);
@@ -385,7 +497,7 @@ static int dslash_step(const Solve &S, DslashArgs d, bool use64) {
     int rc = launch_dslash(S.ctx, S.fat, S.naik, use64, d, nullptr, S.st);
     if (S.timing) {
         cudaEventRecord(e1, S.st);
-        S.events->push_back({e0, e1});
+        (use64 ? S.events64 : S.events)->push_back({e0, e1});
     }
     return rc;
 }
@@ -427,16 +539,40 @@ static int enqueue_iteration_head(const Solve &S) {
     d.parity = 1;
     d.epi = EPI_PLAIN;
     d.active = S.w->st->active;
-    HISQ_CHECK(dslash_step(S, d, false));
+    const bool sloppy64 = S.prec == HISQ_FP64;  // plain FP64 CG reads the FP64 link copy
+    HISQ_CHECK(dslash_step(S, d, sloppy64));
     d.in = S.w->t;
     d.out = S.w->Ap;
     d.parity = 0;
     d.epi = EPI_AOP;
     d.mass2 = S.mass * S.mass;
     d.axpy_in = S.w->p;
-    d.hook = HOOK_ALPHA;
-    HISQ_CHECK(dslash_step(S, d, false));
+    d.hook = S.pc ? HOOK_FCG_ALPHA : HOOK_ALPHA;
+    HISQ_CHECK(dslash_step(S, d, sloppy64));
     return blas(S, HOOK_DECIDE);
+}
+
+// flexible CG: z = M r (network); beta; p = z + beta p with <p, r>; then the CG head
+static int enqueue_fcg_head(const Solve &S) {
+    HISQ_CHECK(pc_forward(S.ctx, S.pc, S.fat, S.naik, S.w->r_lo, S.w->z, S.n, S.st));
+    HISQ_CHECK(blas(S, HOOK_FCG_BETA));
+    HISQ_CHECK(blas(S, HOOK_FCG_PR));
+    return enqueue_iteration_head(S);
+}
+
+static int enqueue_head(const Solve &S) { return S.pc ? enqueue_fcg_head(S) : enqueue_iteration_head(S); }
+
+// end of an iteration: plain CG updates p here; flexible CG only advances the loop
+static int enqueue_tail(const Solve &S) {
+    if (!S.pc) return blas(S, HOOK_LOOP);
+    RedArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.counter = S.w->counter;
+    ra.hook = HOOK_LOOP;
+    ra.st = S.w->st;
+    loop_hook_kernel<<<1, 32, 0, S.st>>>(ra, S.n);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
 }
 
 static int enqueue_setup(const Solve &S) {
@@ -452,7 +588,7 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->n = S.n;
     h->max_iter = P.max_iter;
     h->inner_fp64 = S.prec == HISQ_FP64;
-    h->use_pc = 0;
+    h->use_pc = S.pc != nullptr;
     h->stall_window = P.stall_window;
     h->stall_factor = P.stall_factor;
     h->tol = tol;
@@ -515,9 +651,9 @@ static int build_graph(const Solve &S) {
     if (rc == HISQ_OK) {
         e = cudaStreamBeginCaptureToGraph(cap, while_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "loop capture failed: %s", cudaGetErrorString(e));
-        if (rc == HISQ_OK) rc = enqueue_iteration_head(C);
+        if (rc == HISQ_OK) rc = enqueue_head(C);
         if (rc == HISQ_OK) rc = add_conditional(cap, h_upd, cudaGraphCondTypeIf, &if_body);
-        if (rc == HISQ_OK) rc = blas(C, HOOK_LOOP);
+        if (rc == HISQ_OK) rc = enqueue_tail(C);
         e = cudaStreamEndCapture(cap, &outg);
         if (rc == HISQ_OK && e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "loop capture failed: %s", cudaGetErrorString(e));
     }
@@ -545,7 +681,7 @@ static int build_graph(const Solve &S) {
     w->gc.mass = S.mass;
     w->gc.n = S.n;
     w->gc.prec = S.prec;
-    w->gc.pc = nullptr;
+    w->gc.pc = S.pc;
     return HISQ_OK;
 }
 
@@ -558,7 +694,7 @@ static int solve_bundle(Solve &S, double tol) {
     bool graph = P.use_graph && !S.timing;
     if (graph) {
         bool reuse = w->gc.exec && w->gc.fat == S.fat && w->gc.naik == S.naik && w->gc.mass == S.mass &&
-                     w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == nullptr;
+                     w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == S.pc;
         unsigned long long hl = w->h_st->h_loop, hu = w->h_st->h_upd;
         if (!reuse) {
             HISQ_CHECK(build_graph(S));
@@ -577,9 +713,9 @@ static int solve_bundle(Solve &S, double tol) {
     HISQ_CHECK(enqueue_setup(S));
     int check = std::max(1, P.check_every);
     for (int it = 0; it < P.max_iter; it++) {
-        HISQ_CHECK(enqueue_iteration_head(S));
+        HISQ_CHECK(enqueue_head(S));
         HISQ_CHECK(enqueue_update(S));
-        HISQ_CHECK(blas(S, HOOK_LOOP));
+        HISQ_CHECK(enqueue_tail(S));
         if ((it + 1) % check == 0 || it + 1 == P.max_iter) {
             // the per-iteration residual/flag read-back
             HISQ_CUDA(cudaMemcpyAsync(&w->h_st->any_active, &w->st->any_active, sizeof(int), cudaMemcpyDeviceToHost, S.st));
@@ -636,10 +772,15 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
     if (prec != HISQ_FP64 && fat->prec != prec)
         return set_error(HISQ_ERR_ARG, "inner precision %d needs links packed in that precision (links are %d)", prec, fat->prec);
     if (fat->prec != naik->prec) return set_error(HISQ_ERR_ARG, "fat and Naik links have different precisions");
-    if (P.pc) return set_error(HISQ_ERR_ARG, "flexible CG is driven by hisq_fcg (preconditioner set)");
+    if (P.pc) {
+        if (prec != HISQ_FP32 || fat->prec != HISQ_FP32)
+            return set_error(HISQ_ERR_ARG, "flexible CG with the network needs FP32 inner precision and FP32 links");
+        if (P.pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
+    }
     int bundle = P.bundle > 0 ? P.bundle : std::min(nrhs, HISQ_MAX_BUNDLE);
     bundle = std::min(bundle, nrhs);
-    HISQ_CHECK(ensure_workspace(ctx, bundle, prec, false));
+    HISQ_CHECK(ensure_workspace(ctx, bundle, prec, P.pc != nullptr));
+    if (P.pc) HISQ_CHECK(pc_prepare(ctx, P.pc, bundle));
     Workspace *w = ctx->ws;
     const int Vh = ctx->geom.Vh;
     const size_t vbytes = (size_t)Vh * 6 * sizeof(double);
@@ -650,12 +791,13 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
     memset(&stats, 0, sizeof(stats));
     stats.nrhs = nrhs;
     stats.bundle_size = bundle;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events, events64;
     int worst = HISQ_OK;
 
     for (int k0 = 0; k0 < nrhs; k0 += bundle) {
         int n = std::min(bundle, nrhs - k0);
-        Solve S{ctx, w, fat, naik, n, prec, mass, ctx->stream, P.time_kernels != 0, &events};
+        Solve S{ctx, w, fat, naik, n, prec, mass, ctx->stream, P.time_kernels != 0 && !P.use_graph, &events, &events64,
+                P.pc};
         // tune (outside any capture) before the first use of this shape
         if (P.autotune) {
             tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64);
@@ -683,17 +825,25 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
             else if (worst == HISQ_OK) worst = HISQ_ERR_NOT_CONVERGED;
         }
         stats.fallbacks += h.fallbacks;
+        // setup (pack, init) and unpack, plus per iteration two Dslash, the update and the
+        // p-update; the three residual-recomputation kernels run when an update is due (graph)
+        // or are launched every iteration as gated no-ops (host-driven)
+        bool graph_mode = P.use_graph && !S.timing;
+        long per_iter = P.pc ? 4 + 5 + 3 : 4;  // flexible CG adds 5 network layers, beta and loop kernels
+        stats.kernel_launches += 3 + per_iter * h.bundle_iters + 3L * (graph_mode ? h.update_rounds : h.bundle_iters);
         stats.bundle_iterations += bmax;
         stats.bundles++;
     }
-    for (auto &e : events) {
-        float ms = 0;
-        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
-            stats.dslash_ms += ms;
-            stats.dslash_launches++;
+    for (int which = 0; which < 2; which++) {
+        for (auto &e : which ? events64 : events) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+                (which ? stats.dslash64_ms : stats.dslash_ms) += ms;
+                (which ? stats.dslash64_launches : stats.dslash_launches)++;
+            }
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
         }
-        cudaEventDestroy(e.first);
-        cudaEventDestroy(e.second);
     }
     stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (worst == HISQ_ERR_NOT_CONVERGED)

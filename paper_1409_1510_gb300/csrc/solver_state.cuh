@@ -14,8 +14,9 @@ enum Hook {
     HOOK_DECIDE = 3,    // dots = |r|^2 after the update: beta or reliable update
     HOOK_RELIABLE = 4,  // dots = |b - A x_hi|^2 (FP64): convergence, restart of r
     HOOK_LOOP = 5,      // no dots: advance the iteration counter, set the loop condition
-    HOOK_FCG_ALPHA = 6, // dots = <p, A p>, <p, r> (complex): alpha for flexible CG
-    HOOK_FCG_BETA = 7,  // dots = <r - r_old, z>, <r, z>: beta for flexible CG
+    HOOK_FCG_ALPHA = 6, // dots = <p, A p>; with <p, r> from HOOK_FCG_PR: alpha for flexible CG
+    HOOK_FCG_BETA = 7,  // dots = <r - r_old, z> (complex): beta for flexible CG
+    HOOK_FCG_PR = 8,    // dots = <p, r> (complex) of the new direction
 };
 
 struct SolverState {
@@ -24,6 +25,7 @@ struct SolverState {
     double alpha[HISQ_MAX_BUNDLE][2]; // complex (imaginary part 0 for plain CG)
     double beta[HISQ_MAX_BUNDLE][2];
     double rp_old[HISQ_MAX_BUNDLE][2];// flexible CG: <r_{k-1}, p_{k-1}>
+    double pr[HISQ_MAX_BUNDLE][2];    // flexible CG: <p_k, r_k>
     double r_upd[HISQ_MAX_BUNDLE];    // |r| at the last FP64 residual recomputation
     double r_win[HISQ_MAX_BUNDLE];    // flexible CG: |r| at the start of the stall window
     double bnorm[HISQ_MAX_BUNDLE];
@@ -35,8 +37,10 @@ struct SolverState {
     int status[HISQ_MAX_BUNDLE];
     int win_start[HISQ_MAX_BUNDLE];   // flexible CG: iteration where the stall window began
     int fallback[HISQ_MAX_BUNDLE];    // flexible CG: 1 once switched to plain CG
+    int restart[HISQ_MAX_BUNDLE];     // flexible CG: next direction starts afresh (beta = 0)
     int fallbacks;
     int any_update;
+    int update_rounds;                // iterations that ran the FP64 residual recomputation
     int any_active;
     int bundle_iters;
     int n;
@@ -71,6 +75,7 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             st->r_win[k] = sqrt(b2);
             st->win_start[k] = 0;
             st->fallback[k] = 0;
+            st->restart[k] = 1;
             st->iters[k] = 0;
             st->updates[k] = 0;
             st->update[k] = 0;
@@ -85,6 +90,7 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
         }
         for (int k = n; k < HISQ_MAX_BUNDLE; k++) { st->active[k] = 0; st->update[k] = 0; }
         st->fallbacks = 0;
+        st->update_rounds = 0;
         st->any_active = any;
         st->any_update = 0;
         st->bundle_iters = 0;
@@ -106,11 +112,11 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
         break;
     }
     case HOOK_FCG_ALPHA: {
-        // dots[2k] = <p, A p> (real part), dots[2k+1] unused; dots[2n + 2k (+1)] = <p, r>
+        // dots[k] = <p, A p>; alpha = <p, r> / <p, A p> (complex); <r, p> kept for the next beta
         for (int k = 0; k < n; k++) {
             if (!st->active[k]) continue;
-            double pap = dots[2 * k];
-            double pr_re = dots[2 * n + 2 * k], pr_im = dots[2 * n + 2 * k + 1];
+            double pap = dots[k];
+            double pr_re = st->pr[k][0], pr_im = st->pr[k][1];
             if (!(pap > 0.0) || !isfinite(pap) || !isfinite(pr_re) || !isfinite(pr_im)) {
                 st->active[k] = 0;
                 st->status[k] = RHS_BREAKDOWN;
@@ -121,6 +127,35 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             st->alpha[k][1] = pr_im / pap;
             st->rp_old[k][0] = pr_re;   // <r, p> = conj(<p, r>)
             st->rp_old[k][1] = -pr_im;
+        }
+        break;
+    }
+    case HOOK_FCG_PR: {
+        for (int k = 0; k < n; k++) {
+            st->pr[k][0] = dots[2 * k];
+            st->pr[k][1] = dots[2 * k + 1];
+        }
+        break;
+    }
+    case HOOK_FCG_BETA: {
+        // beta = <r_k - r_{k-1}, z_k> / <r_{k-1}, p_{k-1}> (Polak-Ribiere form of flexible CG);
+        // zero on the first iteration and when the direction restarts (stall fallback)
+        for (int k = 0; k < n; k++) {
+            if (!st->active[k]) continue;
+            if (st->restart[k]) {
+                st->beta[k][0] = st->beta[k][1] = 0.0;
+                st->restart[k] = 0;
+                continue;
+            }
+            double nr = dots[2 * k], ni = dots[2 * k + 1];
+            double dr = st->rp_old[k][0], di = st->rp_old[k][1];
+            double den = dr * dr + di * di;
+            if (!(den > 0.0) || !isfinite(nr) || !isfinite(ni)) {
+                st->beta[k][0] = st->beta[k][1] = 0.0;
+                continue;
+            }
+            st->beta[k][0] = (nr * dr + ni * di) / den;
+            st->beta[k][1] = (ni * dr - nr * di) / den;
         }
         break;
     }
@@ -156,11 +191,13 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
                     st->win_start[k] = st->iters[k];
                 } else if (st->iters[k] - st->win_start[k] >= st->stall_window) {
                     st->fallback[k] = 1;
+                    st->restart[k] = 1;
                     st->fallbacks += 1;
                 }
             }
         }
         st->any_update = any;
+        st->update_rounds += any;
         set_condition(st->h_upd, any);
         break;
     }

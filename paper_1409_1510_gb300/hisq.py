@@ -40,7 +40,9 @@ class hisq_solve_stats(ctypes.Structure):
                 ("total_iterations", ctypes.c_long), ("bundle_iterations", ctypes.c_long),
                 ("reliable_updates", ctypes.c_int), ("fallbacks", ctypes.c_int),
                 ("seconds", ctypes.c_double), ("dslash_ms", ctypes.c_double),
-                ("dslash_launches", ctypes.c_int), ("flops", ctypes.c_double)]
+                ("dslash_launches", ctypes.c_int), ("dslash64_ms", ctypes.c_double),
+                ("dslash64_launches", ctypes.c_int), ("flops", ctypes.c_double),
+                ("kernel_launches", ctypes.c_long)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -76,9 +78,9 @@ _SIGNATURES = {
     "hisq_pc_set_weights": ([_VP, _VP], _I),
     "hisq_pc_get_weights": ([_VP, _VP], _I),
     "hisq_pc_apply": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
-    "hisq_pc_loss_grad": ([_VP, _VP, _VP, _VP, _VP, _I, _VP, _VP], _I),
+    "hisq_pc_loss_grad": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _VP, _VP], _I),
     "hisq_pc_adam_step": ([_VP, _VP, _I, _D, _D, _D, _D], _I),
-    "hisq_pc_train": ([_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _D, _VP], _I),
+    "hisq_pc_train": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _I, _I, _D, _VP], _I),
 }
 
 
@@ -239,9 +241,10 @@ def hisq_pc_apply(pc, fat, naik, vin, vout, nrhs: int):
     _check(load().hisq_pc_apply(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
 
 
-def hisq_pc_loss_grad(pc, fat, naik, r, e, K: int, grad):
+def hisq_pc_loss_grad(pc, fat, naik, mass: float, r, e, K: int, grad):
     loss = _D()
-    _check(load().hisq_pc_loss_grad(pc, fat, naik, _ptr(r), _ptr(e), int(K), ctypes.byref(loss), _ptr(grad)))
+    _check(load().hisq_pc_loss_grad(pc, fat, naik, float(mass), _ptr(r), _ptr(e), int(K), ctypes.byref(loss),
+                                    _ptr(grad)))
     return loss.value
 
 
@@ -249,6 +252,7 @@ def hisq_pc_adam_step(pc, grad, step: int, lr: float, beta1=0.9, beta2=0.999, ep
     _check(load().hisq_pc_adam_step(pc, _ptr(grad), int(step), float(lr), float(beta1), float(beta2), float(eps)))
 
 
-def hisq_pc_train(pc, fat, naik, r, e, K: int, batch: int, epochs: int, lr: float, loss_history=None):
-    _check(load().hisq_pc_train(pc, fat, naik, _ptr(r), _ptr(e), int(K), int(batch), int(epochs), float(lr),
-                                _ptr(loss_history)))
+def hisq_pc_train(pc, fat, naik, mass: float, r, e, K: int, batch: int, epochs: int, lr: float,
+                  loss_history=None):
+    _check(load().hisq_pc_train(pc, fat, naik, float(mass), _ptr(r), _ptr(e), int(K), int(batch), int(epochs),
+                                float(lr), _ptr(loss_history)))

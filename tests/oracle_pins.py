@@ -213,6 +213,22 @@ def network_weights_aop(mass):
     return np.concatenate([W1.ravel(), W2.ravel(), W3.ravel()])
 
 
+def pin_network_loss_zero_at_inverse(make, dims=(4, 4, 4, 4), mass=0.4, tol=1e-12):
+    """The loss vanishes for pairs the network maps exactly: with the weights that spell out A,
+    the pairs (r, e) = (v, A v) give M r = e, so loss = 0; scaling e by 1/2 gives exactly
+    |A (A v / 2)|^2 / |v|^2 per pair (a closed form of the residual-norm loss)."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    W = network_weights_aop(mass)
+    v = np.stack([hi.gaussian_rhs(lat, 30 + k) for k in range(2)])
+    Av = o.aop(v, mass)
+    l0, _ = o.pc_loss_grad(W, v, Av, mass, False)
+    l1, _ = o.pc_loss_grad(W, v, 0.5 * Av, mass, False)
+    AAv = o.aop(0.5 * Av, mass)
+    want = np.mean([np.vdot(AAv[k], AAv[k]).real / np.vdot(v[k], v[k]).real for k in range(2)])
+    return l0 <= tol and abs(l1 - want) <= 1e-12 * want, f"zero {l0:.1e}, closed form {abs(l1 - want) / want:.1e}"
+
+
 def pin_network_special_weights(make, dims=(8, 4, 4, 6), mass=0.2, tol=1e-13):
     """Identity weights give the identity; the weights that spell out Eq. (3) twice give A."""
     lat, X, N = _fields(dims)
@@ -247,7 +263,8 @@ def pin_network_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=24, tol=1e-6):
     W = _rand_vec(rng, o.pc_num_weights) * 0.3
     r = np.stack([hi.gaussian_rhs(lat, 10 + k) for k in range(2)])
     e = np.stack([hi.gaussian_rhs(lat, 20 + k) for k in range(2)])
-    _, g = o.pc_loss_grad(W, r, e)
+    mass = 0.3
+    _, g = o.pc_loss_grad(W, r, e, mass)
     h = 1e-5
     worst = 0.0
     for i in rng.choice(W.size, n_checks, replace=False):
@@ -255,7 +272,7 @@ def pin_network_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=24, tol=1e-6):
             Wp, Wm = W.copy(), W.copy()
             Wp[i] += unit * h
             Wm[i] -= unit * h
-            fd = (o.pc_loss_grad(Wp, r, e, False)[0] - o.pc_loss_grad(Wm, r, e, False)[0]) / (2 * h)
+            fd = (o.pc_loss_grad(Wp, r, e, mass, False)[0] - o.pc_loss_grad(Wm, r, e, mass, False)[0]) / (2 * h)
             worst = max(worst, abs(fd - comp) / max(abs(comp), 1e-3 * np.abs(g).max()))
     return worst <= tol, f"worst rel {worst:.2e}"
 
@@ -277,6 +294,6 @@ def pin_fcg_identity_is_cg(make, dims=(4, 4, 4, 6), mass=0.1, tol=1e-10):
 ALL_PINS = [
     pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
     pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
-    pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd,
+    pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd, pin_network_loss_zero_at_inverse,
     pin_fcg_identity_is_cg,
 ]

@@ -125,3 +125,14 @@ def test_device_pointers_and_timing():
         x = xd.cpu().numpy().view(np.complex128)
         assert g.oracle.true_residual(b, x, 0.05)[0] <= TOL * SLACK
         assert stats.dslash_launches >= 2 * stats.max_iterations and stats.dslash_ms > 0
+
+
+def test_plain_fp64_cg_on_lower_precision_links():
+    """inner_prec FP64 with links packed in FP16 runs on the handle's FP64 copy."""
+    dims = (8, 10, 8, 6)
+    with gpu(dims, 2) as g:
+        b = hi.gaussian_rhs(g.lat, 9)
+        x, stats, iters, res = _solve(g, [b], 0.05, inner_prec=0)
+        assert g.oracle.true_residual(b, x[0], 0.05)[0] <= TOL * SLACK
+        _, it_oracle, _ = g.oracle.cg(b, 0.05, TOL)
+        assert abs(int(iters[0]) - it_oracle) <= 2
