@@ -126,6 +126,32 @@ int hisq_dslash(const hisq_links *fat, const hisq_links *naik, const void *in, v
 int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
              void *out, int nrhs, double *pAp);
 
+/* ---- A-operator without allocation ---------------------------------------------------------- */
+
+/* Size of the static device scratch behind hisq_aop_noalloc (per device, held until exit). */
+#define HISQ_AOP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* hisq_aop without any device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc -- code whose device memory is owned by another
+ * allocator (a framework's caching pool or a fixed budget that must not be exceeded behind its
+ * back), code on a latency-critical path that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation, and code that must not fail with an out-of-memory error in the middle of a
+ * run.  It computes the same out and pAp as hisq_aop (same kernels, a fixed launch shape instead
+ * of the autotuned one), but its scratch -- the odd-parity intermediate, the reduction partials and
+ * the block counter -- lives in one file-scope static __device__ array of
+ * HISQ_AOP_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library holds until the
+ * process exits.  The caller still passes in and out (device, internal layout in the links'
+ * precision) and pAp (host or device, nrhs doubles, may be NULL).
+ * Limits: the odd-parity intermediate (hisq_vector_bytes(prec, nrhs)) must fit in the scratch
+ * less 1 MiB of reduction space, e.g. FP32 32^3x8 up to nrhs = 4; larger requests return
+ * HISQ_ERR_ARG with a message naming the limit, and nothing is launched.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares the
+ * one array and leaves its contents behind (the block counter is cleared at the start of each
+ * call): calls that overlap on the GPU, from several streams or host threads, race. */
+int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
+                     void *out, int nrhs, double *pAp);
+
 /* ---- solvers (rows a4-a6, a9) ------------------------------------------------------------- */
 
 typedef struct {

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "hisq_unpack": ([_VP, _VP, _I, _I], _I),
     "hisq_dslash": ([_VP, _VP, _VP, _VP, _I, _I], _I),
     "hisq_aop": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
+    "hisq_aop_noalloc": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
     "hisq_default_solver_params": ([ctypes.POINTER(hisq_solver_params)], None),
     "hisq_set_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
@@ -174,6 +175,11 @@ def hisq_dslash(fat, naik, vin, vout, nrhs: int, parity: int):
 
 def hisq_aop(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
     _check(load().hisq_aop(fat, naik, float(mass), _ptr(vin), _ptr(vout), int(nrhs), _ptr(pAp)))
+
+
+def hisq_aop_noalloc(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
+    """hisq_aop with its scratch in a static device array: allocates nothing (see include/hisq.h)."""
+    _check(load().hisq_aop_noalloc(fat, naik, float(mass), _ptr(vin), _ptr(vout), int(nrhs), _ptr(pAp)))
 
 
 def hisq_default_solver_params() -> hisq_solver_params:
