@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--dims", default="32,32,32,8")
     ap.add_argument("--mass", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="cg", choices=["cg", "sweep", "learned"],
+                    help="cg: the benchmark line; sweep: Dslash throughput against the number of "
+                         "right-hand sides; learned: the learned-preconditioner workload")
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--test-rhs", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=30)
     return ap.parse_args()
 
 
@@ -363,6 +369,25 @@ def run_ours(args, rank, world, local_rank, dist):
         hisq.hisq_links_destroy(fv)
         hisq.hisq_links_destroy(nv)
 
+    # ---- the same solve for a bundle of 16 right-hand sides sharing every link read (Eq. (4)) ----
+    nb = 16
+    bs = [d64(hi.gaussian_rhs(lat, 100 + k)) for k in range(nb)]
+    xs = [torch.zeros_like(v) for v in bs]
+    set_params(inner, 1)
+    bms = []
+    for rep in range(4):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hisq.hisq_cg_solve(fat, naik, bs, xs, args.mass, TOL)
+        e1.record(stream)
+        e1.synchronize()
+        bms.append(e0.elapsed_time(e1))
+    bst = hisq.hisq_last_stats()
+    batched = {"nrhs": nb, "s_per_rhs": statistics.median(bms[1:]) / 1e3 / nb,
+               "max_iterations": bst.max_iterations, "converged": bst.converged}
+
     # ---- end to end through the C ABI with pinned host buffers ----
     ke = max(3, min(args.steps, 20))
     ems, est = timed(ke, inner, 1, host=True)
@@ -385,6 +410,7 @@ def run_ours(args, rank, world, local_rank, dist):
             "dslash": {"gflops": dslash_gflops, "hbm_gbs": achieved, "precision": args.inner,
                        "fp64_residual_dslash_gflops": fp64_dslash_gflops, "nrhs": 1},
             "host_driven_ms_per_step": host_ms, "other_inner_precisions": variants,
+            "bundle_of_16": dict(batched, speedup_per_rhs_vs_single=s_rhs / batched["s_per_rhs"]),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFlop/s", "h2d_bytes_per_step": vbytes, "d2h_bytes_per_step": vbytes},
             "gpu_launches": int(launches_all), "clocks": clk.summary(), "wall_s_timed_region": t_wall,
@@ -393,8 +419,169 @@ def run_ours(args, rank, world, local_rank, dist):
     return line
 
 
+def run_sweep(args):
+    """Dslash GFlop/s and GB/s against n (Eq. (4)) for each storage precision, 18-real links,
+    autotuned launch shape, L2 flushed before every timed launch (CUDA events)."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import accounting as acc
+    from paper_1409_1510_gb300 import hisq
+    dims, _ = workload(args)
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    hisq.hisq_init(dims, 0, stream)
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    hbm_peak, _ = peaks()
+    rows = []
+    for name in ("fp32", "fp16", "bf16", "fp64"):
+        prec = PREC[name]
+        fat = hisq.hisq_links_create(d64(X), False, prec, 18)
+        naik = hisq.hisq_links_create(d64(N), True, prec, 18)
+        for n in ((1, 2, 4, 8, 12, 16) if prec else (1, 2, 4)):
+            vin = torch.empty(hisq.hisq_vector_bytes(prec, n), dtype=torch.uint8, device=dev)
+            hisq.hisq_pack(d64(np.stack([hi.gaussian_rhs(lat, k) for k in range(n)])), vin, n, prec)
+            vout = torch.empty_like(vin)
+            shape = hisq.hisq_autotune(fat, naik, n)
+            ts = []
+            for i in range(12):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hisq.hisq_dslash(fat, naik, vin, vout, n, i % 2)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            sec = statistics.median(ts[2:]) / 1e3
+            elem = {0: 8, 1: 4, 2: 2, 3: 2}[prec]
+            byts = acc.compulsory_bytes(n, elem, elem, 18, 8.0 if prec in (2, 3) else 0.0,
+                                        4.0 if prec == 2 else 0.0) * lat.half_volume
+            rows.append({"precision": name, "nrhs": n, "us": sec * 1e6,
+                         "gflops": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e9,
+                         "gbs": byts / sec / 1e9, "frac_hbm": byts / sec / 1e9 / hbm_peak,
+                         "shape": {"rhs_per_thread": shape[0], "threads": shape[1], "lanes_per_site": shape[2]}})
+            print(json.dumps(rows[-1]), flush=True)
+        hisq.hisq_links_destroy(fat)
+        hisq.hisq_links_destroy(naik)
+    hisq.hisq_finalize()
+
+
+def run_learned(args):
+    """Learned-preconditioner workload: (r, e) pairs from plain CG iterates on the same gauge
+    field, training on the GPU, then flexible CG against plain CG on fresh right-hand sides."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims, _ = workload(args)
+    mass, tol = args.mass, TOL
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    hisq.hisq_init(dims, 0, stream)
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    fat = hisq.hisq_links_create(d64(X), False, 1, 18)
+    naik = hisq.hisq_links_create(d64(N), True, 1, 18)
+    vh = lat.half_volume
+    p = hisq.hisq_default_solver_params()
+    p.inner_prec = 1
+    hisq.hisq_set_solver_params(p)
+    # pairs: 16 right-hand sides at a time, x* to 1e-10, then x_k after k iterations
+    t0 = time.perf_counter()
+    per_rhs = 25
+    nrhs = (args.pairs + per_rhs - 1) // per_rhs
+    bsz = hisq.hisq_vector_bytes(1, 16)
+    nb = (args.pairs + 15) // 16
+    rbuf = torch.empty(nb * bsz, dtype=torch.uint8, device=dev)
+    ebuf = torch.empty_like(rbuf)
+    pending_r, pending_e, filled = [], [], 0
+    canon = lambda v: torch.stack(v).contiguous()
+    done = 0
+    for j0 in range(0, nrhs, 16):
+        bs = [d64(hi.gaussian_rhs(lat, 7000 + j)) for j in range(j0, min(nrhs, j0 + 16))]
+        xs = [torch.zeros_like(b) for b in bs]
+        p.max_iter = 20000
+        hisq.hisq_set_solver_params(p)
+        hisq.hisq_cg_solve(fat, naik, bs, xs, mass, tol)
+        its = hisq.hisq_last_stats().max_iterations
+        for k in np.linspace(2, max(3, int(0.8 * its)), per_rhs).astype(int):
+            p.max_iter = int(k)
+            hisq.hisq_set_solver_params(p)
+            xk = [torch.zeros_like(b) for b in bs]
+            hisq.hisq_cg_solve(fat, naik, bs, xk, mass, tol, raise_on_error=False)
+            # r_k = b - A x_k on the GPU (A in FP32 through the library)
+            xin = torch.empty(hisq.hisq_vector_bytes(1, len(bs)), dtype=torch.uint8, device=dev)
+            ax = torch.empty_like(xin)
+            hisq.hisq_pack(canon(xk), xin, len(bs), 1)
+            hisq.hisq_aop(fat, naik, mass, xin, ax, len(bs))
+            axc = torch.empty((len(bs), vh, 3, 2), dtype=torch.float64, device=dev)
+            hisq.hisq_unpack(ax, axc, len(bs), 1)
+            for q in range(len(bs)):
+                if done >= args.pairs:
+                    break
+                pending_r.append(bs[q].view(vh, 3, 2) - axc[q])
+                pending_e.append(xs[q].view(vh, 3, 2) - xk[q].view(vh, 3, 2))
+                done += 1
+                if len(pending_r) == 16:
+                    hisq.hisq_pack(canon(pending_r), rbuf[filled * bsz:(filled + 1) * bsz], 16, 1)
+                    hisq.hisq_pack(canon(pending_e), ebuf[filled * bsz:(filled + 1) * bsz], 16, 1)
+                    filled += 1
+                    pending_r, pending_e = [], []
+    pairs = filled * 16
+    t_pairs = time.perf_counter() - t0
+    # training from the identity plus a small random perturbation (the identity is a saddle point)
+    rng = np.random.default_rng(0)
+    w0 = np.zeros(408, complex)
+    w0[[0, 68, 340]] = 1.0
+    w0 += 0.02 * (rng.standard_normal(408) + 1j * rng.standard_normal(408))
+    pc = hisq.hisq_pc_create(np.ascontiguousarray(w0).view(np.float64))
+    hist = np.zeros(args.epochs)
+    t0 = time.perf_counter()
+    hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, pairs, 16, args.epochs, 5e-3, hist)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # fresh right-hand sides: plain CG against flexible CG with the network (both FP32 inner,
+    # FP64 reliable updates, true residual 1e-10 judged in FP64)
+    tests = [d64(hi.gaussian_rhs(lat, 9000 + k)) for k in range(args.test_rhs)]
+    out = {}
+    for name, handle in (("cg", None), ("fcg_learned", pc)):
+        p = hisq.hisq_default_solver_params()
+        p.inner_prec = 1
+        p.pc = handle.value if handle is not None else None
+        p.bundle = 16
+        hisq.hisq_set_solver_params(p)
+        xs = [torch.zeros_like(b) for b in tests]
+        hisq.hisq_cg_solve(fat, naik, tests[:16], xs[:16], mass, tol)  # warm-up / capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hisq.hisq_cg_solve(fat, naik, tests, xs, mass, tol)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        iters = np.zeros(len(tests), dtype=np.int32)
+        res = np.zeros(len(tests))
+        st = hisq.hisq_last_stats(iters, res)
+        out[name] = {"s_per_rhs": el / len(tests), "mean_iterations": float(iters.mean()),
+                     "max_true_residual": float(res.max()), "converged": st.converged,
+                     "fallbacks": st.fallbacks}
+    line = {"mode": "learned", "lattice": dims, "mass": mass, "pairs": pairs, "pair_seconds": t_pairs,
+            "train_seconds": t_train, "epochs": args.epochs, "loss_first": float(hist[0]),
+            "loss_last": float(hist[-1]), "test_rhs": len(tests), **out,
+            "iteration_ratio": out["fcg_learned"]["mean_iterations"] / out["cg"]["mean_iterations"],
+            "time_ratio": out["fcg_learned"]["s_per_rhs"] / out["cg"]["s_per_rhs"]}
+    print(json.dumps(line), flush=True)
+    hisq.hisq_finalize()
+
+
 def main():
     args = parse()
+    if args.mode == "sweep":
+        run_sweep(args)
+        return
+    if args.mode == "learned":
+        run_learned(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -20,12 +20,12 @@
  * whatever X and N it is given, with periodic index arithmetic.
  *
  * Internal vector layout (what hisq_dslash, hisq_aop and the preconditioner read and write):
- *   site-major, colour, right-hand side innermost: element (s, c, r) at index (s*3 + c)*n + r,
- *   one complex number per element, stored as
- *     HISQ_FP64: double2      HISQ_FP32: float2      HISQ_BF16: __nv_bfloat162 (unscaled)
- *     HISQ_FP16: __half2, followed (after the V/2*3*n half2 array, at a 16-byte aligned
- *                offset) by one float scale per (site, rhs), index s*n + r; the value of an
- *                element is half2 * scale.
+ *   site-major with the right-hand sides of a site adjacent:
+ *     HISQ_FP64 / HISQ_FP32 / HISQ_BF16: element (s, c, r) is the complex number at index
+ *                (s*3 + c)*n + r, stored as double2 / float2 / __nv_bfloat162 (BF16 unscaled);
+ *     HISQ_FP16: one 16-byte record per (site, rhs) at index s*n + r: the three colour
+ *                components as __half2 followed by a float scale; value = half * scale, and
+ *                the scale is the largest |real or imaginary part| of the three components.
  *   hisq_vector_bytes() gives the size of one such bundle.
  *
  * Threads and contexts: hisq_init() creates a context bound to the calling host thread (one
@@ -209,15 +209,19 @@ typedef struct {
 int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual);
 
 /* Pick and cache the fastest Dslash launch shape for nrhs right-hand sides in the links'
- * precision (row a6), timing every candidate with CUDA events.  Writes the chosen
- * right-hand sides per thread and threads per block if the pointers are not NULL. */
+ * precision (row a6), timing every candidate with CUDA events after an L2 flush.  Writes the
+ * chosen right-hand sides per thread, threads per block and lanes per site (1, or 2 when the fat
+ * and Naik halves of a site run on two lanes) if the pointers are not NULL.  Allocates its
+ * timing buffers. */
 int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int nrhs, int *rhs_per_thread,
-                  int *block_threads);
+                  int *block_threads, int *lanes_per_site);
 
 /* Pin the Dslash launch shape used for nrhs right-hand sides with links of (prec, recon):
- * rhs_per_thread in {1, 2, 4, 8} dividing nrhs (FP64: 1, 2, 4), block_threads in 32..256.
+ * rhs_per_thread in {1, 2, 4, 8} dividing nrhs (FP64: 1, 2, 4), block_threads in 32..256,
+ * lanes_per_site 1 or 2 (2 only with 18-real Naik links and rhs_per_thread <= 4).
  * Overrides the autotuner's choice for that key. */
-int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_thread, int block_threads);
+int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_thread, int block_threads,
+                          int lanes_per_site);
 
 /* ---- learned preconditioner (rows a7-a9) --------------------------------------------------- */
 

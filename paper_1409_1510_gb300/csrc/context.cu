@@ -243,8 +243,7 @@ __global__ void pack_vec_kernel(int Vh, int n, const double *canon, void *intern
     VecView<P> v;
     v.data = internal;
     v.n = n;
-    v.scale = P == HISQ_FP16 ? reinterpret_cast<float *>(reinterpret_cast<char *>(internal) + fp16_scale_offset(Vh, n)) : nullptr;
-    store_site<P>(v, s, r, w);
+    store_vec<P>(v, s, r, w);
 }
 
 template <int P>
@@ -255,11 +254,10 @@ __global__ void unpack_vec_kernel(int Vh, int n, const void *internal, double *c
     VecView<P> v;
     v.data = const_cast<void *>(internal);
     v.n = n;
-    v.scale = P == HISQ_FP16 ? reinterpret_cast<float *>(reinterpret_cast<char *>(const_cast<void *>(internal)) + fp16_scale_offset(Vh, n)) : nullptr;
-    Cplx<typename Prec<P>::real> w[1][3];
-    load_site<P, 1>(v, s, r, 1, w);
+    Cplx<typename Prec<P>::real> w[3];
+    load_vec<P>(v, s, r, w);
     double *c = canon + ((size_t)r * Vh + s) * 6;
-    for (int k = 0; k < 3; k++) { c[2 * k] = (double)w[0][k].re; c[2 * k + 1] = (double)w[0][k].im; }
+    for (int k = 0; k < 3; k++) { c[2 * k] = (double)w[k].re; c[2 * k + 1] = (double)w[k].im; }
 }
 
 int pack_vectors(hisq_ctx *ctx, const double *canon_dev, void *internal, int n, int prec, cudaStream_t st) {
@@ -301,7 +299,7 @@ LaunchShape default_shape(int prec, int n) {
     int maxR = prec == HISQ_FP64 ? 2 : 4;
     for (int c = maxR; c >= 1; c /= 2)
         if (n % c == 0) { R = c; break; }
-    return {R, 256};
+    return {R, 256, 1};
 }
 
 static int pow2_floor(int x) {
@@ -311,16 +309,21 @@ static int pow2_floor(int x) {
 }
 
 int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, bool use64, const DslashArgs &d,
-                  const LaunchShape *shape, cudaStream_t stream) {
+                  const LaunchShape *shape, cudaStream_t stream, int *grid_out) {
     int prec = use64 ? HISQ_FP64 : fat->prec;
     int recon = use64 ? 18 : naik->recon;
     LaunchShape sh = shape ? *shape : tuned_shape(ctx, fat, naik, d.n, use64);
     int R = sh.R;
     if (R != 1 && R != 2 && R != 4 && R != 8) R = 1;
     if (d.n % R != 0) R = 1;
+    if (prec == HISQ_FP64 && R > 4) R = 4;  // FP64 kernels are built for up to four RHS per thread
+    int S = (sh.S == 2 && recon == 18 && R <= 4) ? 2 : 1;
     int t = (d.n + R - 1) / R;
-    int spb = pow2_floor(std::max(1, std::min(sh.threads, 256) / t));  // kernels are bounded to 256 threads
-    int threads = spb * t;
+    // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
+    // threads keep both the partial count and that block's share of the sum small
+    int want_threads = d.epi != EPI_PLAIN ? std::max(sh.threads, 128) : sh.threads;
+    int spb = pow2_floor(std::max(1, std::min(want_threads, 256) / (S * t)));  // kernels are bounded to 256 threads
+    int threads = (spb * S * t + 31) / 32 * 32;  // whole warps; threads with site index >= spb idle
     if (threads > 256) return set_error(HISQ_ERR_ARG, "launch shape of %d threads is too large", threads);
 
     KArgs a;
@@ -346,10 +349,11 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     a.red.dot_out = d.dot_out;
     a.red.hook = d.hook;
     a.red.st = reinterpret_cast<SolverState *>(d.hook_state);
+    a.red.partials_only = d.partials_only;
 
     size_t smem = 0;
     if (d.epi != EPI_PLAIN) {
-        size_t need = std::max((size_t)spb * d.n, (size_t)threads);
+        size_t need = std::max((size_t)spb * d.n, (size_t)threads + 64);
         smem = need * sizeof(double);
         long tiles = (ctx->geom.Vh + spb - 1) / spb;
         // the grid never exceeds one resident wave per SM times 64, nor the tile count
@@ -360,12 +364,13 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int grid = 0;
     cudaError_t e;
     switch (prec) {
-    case HISQ_FP64: e = launch_dslash_prec<HISQ_FP64>(a, recon, d.epi, R, threads, smem, ctx->num_sms, stream, &grid); break;
-    case HISQ_FP32: e = launch_dslash_prec<HISQ_FP32>(a, recon, d.epi, R, threads, smem, ctx->num_sms, stream, &grid); break;
-    case HISQ_FP16: e = launch_dslash_prec<HISQ_FP16>(a, recon, d.epi, R, threads, smem, ctx->num_sms, stream, &grid); break;
-    default: e = launch_dslash_prec<HISQ_BF16>(a, recon, d.epi, R, threads, smem, ctx->num_sms, stream, &grid); break;
+    case HISQ_FP64: e = launch_dslash_prec<HISQ_FP64>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
+    case HISQ_FP32: e = launch_dslash_prec<HISQ_FP32>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
+    case HISQ_FP16: e = launch_dslash_prec<HISQ_FP16>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
+    default: e = launch_dslash_prec<HISQ_BF16>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
     }
     if (e != cudaSuccess) return set_error(HISQ_ERR_CUDA, "Dslash launch failed: %s", cudaGetErrorString(e));
+    if (grid_out) *grid_out = grid;
     return HISQ_OK;
 }
 

@@ -4,11 +4,11 @@
 namespace hisq {
 
 template <>
-cudaError_t launch_dslash_prec<HISQ_FP16>(const KArgs &a, int recon, int epi, int R, int threads, size_t smem,
+cudaError_t launch_dslash_prec<HISQ_FP16>(const KArgs &a, int recon, int epi, int R, int S, int threads, size_t smem,
                                         int num_sms, cudaStream_t s, int *grid) {
-    if (recon == 13) return launch_epi<HISQ_FP16, 13>(a, epi, R, threads, smem, num_sms, s, grid);
-    if (recon == 9) return launch_epi<HISQ_FP16, 9>(a, epi, R, threads, smem, num_sms, s, grid);
-    return launch_epi<HISQ_FP16, 18>(a, epi, R, threads, smem, num_sms, s, grid);
+    if (recon == 13) return launch_epi<HISQ_FP16, 13>(a, epi, R, S, threads, smem, num_sms, s, grid);
+    if (recon == 9) return launch_epi<HISQ_FP16, 9>(a, epi, R, S, threads, smem, num_sms, s, grid);
+    return launch_epi<HISQ_FP16, 18>(a, epi, R, S, threads, smem, num_sms, s, grid);
 }
 
 }  // namespace hisq

@@ -24,6 +24,7 @@ struct RedArgs {
     double *dot_out;       // [ndots] final dots (may be null)
     int hook;              // solver hook run by the last block (HOOK_NONE = none)
     SolverState *st;
+    int partials_only;     // 1: publish the block partials and stop (a later kernel sums them)
 };
 
 struct KArgs {
@@ -44,36 +45,38 @@ struct KArgs {
 
 template <int P>
 __device__ __forceinline__ VecView<P> view(const void *base, int Vh, int n) {
+    (void)Vh;
     VecView<P> v;
     v.data = const_cast<void *>(base);
     v.n = n;
-    v.scale = (P == HISQ_FP16 && base)
-                  ? reinterpret_cast<float *>(reinterpret_cast<char *>(const_cast<void *>(base)) + fp16_scale_offset(Vh, n))
-                  : nullptr;
     return v;
 }
 
-// Deterministic reduction of red[rows][ndots] (shared, rows a power of two) into per-block
-// partials, then the last-block-done finish: the block that takes the last ticket sums the
-// partials of all blocks in a fixed order, writes dot_out and runs the hook for a bundle of
-// hook_n right-hand sides.  No block ever waits for another.  All threads of the block call it;
-// ndots may be 0 (hook only).  red must hold max(rows * ndots, blockDim.x) doubles.
+// Deterministic reduction of red[rows][ndots] (shared) into per-block partials, then the
+// last-block-done finish: the block that takes the last ticket sums the partials of all blocks
+// in a fixed order, writes dot_out and runs the hook for a bundle of hook_n right-hand sides.
+// No block ever waits for another.  All threads of the block call it; blockDim.x is a multiple
+// of 32; ndots may be 0 (hook only); red holds at least blockDim.x + 64 doubles, and 2 * ndots
+// when ndots > 64.  Block column sums run one warp per column (lanes stride over the rows and
+// finish with a shuffle tree); the last block gives each thread one column and a stride of the
+// blocks' partials, so each stage needs a single barrier.
 __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int ndots, int hook_n, const RedArgs &ra) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    __shared__ int is_last;
     if (ndots > 0) {
-        for (int stride = rows / 2; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int i = tid; i < stride * ndots; i += blockDim.x) {
-                int row = i / ndots, j = i - row * ndots;
-                red[row * ndots + j] += red[(row + stride) * ndots + j];
+        __syncthreads();
+        for (int j = warp; j < ndots; j += nwarps) {
+            double s = 0.0;
+            for (int row = lane; row < rows; row += 32) s += red[row * ndots + j];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) {
+                ra.partials[(size_t)blockIdx.x * ndots + j] = s;
+                if (!ra.partials_only) __threadfence();  // publish before the ticket is taken
             }
         }
-        __syncthreads();
-        for (int j = tid; j < ndots; j += blockDim.x) ra.partials[(size_t)blockIdx.x * ndots + j] = red[j];
-        // only the threads that published partials fence them before the ticket is taken
-        if (tid < ndots) __threadfence();
     }
-    __shared__ int is_last;
+    if (ra.partials_only) return;  // the kernel boundary publishes them to the consumer
     __syncthreads();
     if (tid == 0) is_last = (atomicAdd(ra.counter, 1u) == gridDim.x - 1);
     __syncthreads();
@@ -81,34 +84,74 @@ __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int n
     if (tid == 0) __threadfence();
     __syncthreads();
     if (ndots > 0) {
-        int nchunks = 1;
-        while (nchunks * 2 * ndots <= (int)blockDim.x) nchunks *= 2;
-        for (int i = tid; i < nchunks * ndots; i += blockDim.x) {
-            int chunk = i / ndots, j = i - chunk * ndots;
+        const int nb = gridDim.x;
+        if (ndots <= 64) {
+            // thread (k, j), j < np2 (ndots padded to a power of two), sums column j over blocks
+            // k, k + per, ...; lanes of one column are np2 apart in a warp and meet in a shuffle
+            // tree, then at most 8 warp sums per column are added in a fixed order
+            int np2 = 1;
+            while (np2 < ndots) np2 *= 2;
+            const int per = blockDim.x / np2;
+            const int j = tid % np2, k = tid / np2;
             double s = 0.0;
-            for (int b = chunk; b < (int)gridDim.x; b += nchunks) s += __ldcg(ra.partials + (size_t)b * ndots + j);
-            red[chunk * ndots + j] = s;
-        }
-        for (int stride = nchunks / 2; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int i = tid; i < stride * ndots; i += blockDim.x) {
-                int chunk = i / ndots, j = i - chunk * ndots;
-                red[chunk * ndots + j] += red[(chunk + stride) * ndots + j];
+            if (j < ndots && k < per) {
+#pragma unroll 4
+                for (int b = k; b < nb; b += per) s += __ldcg(ra.partials + (size_t)b * ndots + j);
             }
+            for (int off = 16; off >= np2; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            const int groups = np2 < 32 ? nwarps : per;           // partial sums per column
+            if (np2 < 32) {
+                if (lane < np2) red[warp * np2 + lane] = s;
+            } else {
+                red[tid] = s;
+            }
+            __syncthreads();
+            if (tid < ndots) {
+                double t = 0.0;
+                for (int q = 0; q < groups; q++) t += red[q * np2 + tid];
+                red[blockDim.x + tid] = t;
+            }
+            __syncthreads();
+            if (tid < ndots) red[tid] = red[blockDim.x + tid];
+        } else {
+            // many columns (network weight gradients): one thread per column
+            for (int j = tid; j < ndots; j += blockDim.x) {
+                double t = 0.0;
+#pragma unroll 8
+                for (int b = 0; b < nb; b++) t += __ldcg(ra.partials + (size_t)b * ndots + j);
+                red[ndots + j] = t;
+            }
+            __syncthreads();
+            for (int j = tid; j < ndots; j += blockDim.x) red[j] = red[ndots + j];
         }
         __syncthreads();
         if (ra.dot_out)
             for (int j = tid; j < ndots; j += blockDim.x) ra.dot_out[j] = red[j];
     }
+    if (ra.hook && ra.st) {
+        // the scalar step works on a shared-memory copy of the bundle state: one coalesced read
+        // and one write-back instead of a chain of dependent global accesses by one thread
+        __shared__ SolverState sst;
+        constexpr int WORDS = sizeof(SolverState) / sizeof(uint32_t);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(ra.st);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sst);
+#pragma unroll 4
+        for (int i = tid; i < WORDS; i += blockDim.x) dst[i] = __ldcg(src + i);
+        __syncthreads();
+        if (tid == 0) run_hook(ra.hook, &sst, red, hook_n);
+        __syncthreads();
+        uint32_t *back = reinterpret_cast<uint32_t *>(ra.st);
+        for (int i = tid; i < WORDS; i += blockDim.x) back[i] = dst[i];
+    }
     if (tid == 0) {
-        if (ra.hook && ra.st) run_hook(ra.hook, ra.st, red, hook_n);
         *ra.counter = 0u;
         __threadfence();
     }
 }
 
-template <int P, int NR, int R, int EPI>
+template <int P, int NR, int R, int EPI, int S>
 __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
+    static_assert(S == 1 || (S == 2 && NR == 18), "the lane split needs identical fat and Naik encodings");
     using real = typename Prec<P>::real;
     using FatC = LinkCodec<P, 18>;
     using NaikC = LinkCodec<P, NR>;
@@ -118,8 +161,9 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 
     const Geom &g = a.g;
     const int tid = threadIdx.x;
-    const int gi = tid % a.t;
-    const int sl = tid / a.t;
+    const int part = (S == 2) ? (tid & 1) : 0;
+    const int gi = (tid / S) % a.t;
+    const int sl = tid / (S * a.t);
     const int r0 = gi * R;
     const int nvalid = min(R, a.n - r0);
     const VecView<P> vin = view<P>(a.in, g.Vh, a.n);
@@ -139,8 +183,8 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 
     for (int tile = blockIdx.x; (long)tile * a.spb < g.Vh; tile += gridDim.x) {
         const int s = tile * a.spb + sl;
-        if (s >= g.Vh || !any_act) continue;
-        const SiteCoord sc = decode_site(g, s, a.parity);
+        const bool valid = sl < a.spb && s < g.Vh && any_act;
+        if (S == 1 && !valid) continue;
 
         Cplx<real> acc[R][3];
 #pragma unroll
@@ -148,90 +192,101 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
 
-        // ---- fat links: one hop ----
-        real fscale = (real)1;
-        if (a.fat.scale) fscale = (real)__ldg(a.fat.scale + (size_t)a.parity * g.Vh + s);
+        if (valid) {
+            const SiteCoord sc = decode_site(g, s, a.parity);
+            // the kinds this lane applies: S = 1 both, S = 2 fat (part 0) or Naik (part 1)
 #pragma unroll
-        for (int grp = 0; grp < FatC::GROUPS; grp++) {
-            uint32_t u[FatC::WG * 4];
-            FatC::load_group(a.fat, a.parity, g.Vh, s, grp, u);
+            for (int kind = 0; kind < (S == 1 ? 2 : 1); kind++) {
+                const bool naik_kind = (S == 1) ? (kind == 1) : (part == 1);
+                const LinkField f = naik_kind ? a.naik : a.fat;
+                const int hop = naik_kind ? 3 : 1;
+                if (S == 1 && kind == 1 && NR != 18) {
+                    // 13- or 9-real Naik records (S = 1 only)
 #pragma unroll
-            for (int l = 0; l < FatC::G; l++) {
-                const int slot = grp * FatC::G + l;
-                const int mu = slot >> 1;
-                const int nb = neighbour(g, sc, s, mu, (slot & 1) ? -1 : 1);
-                Cplx<real> M[3][3];
-                FatC::decode(u, l, fscale, M);
-                Cplx<real> v[R][3];
+                    for (int grp = 0; grp < NaikC::GROUPS; grp++) {
+                        uint32_t u[NaikC::WG * 4];
+                        NaikC::load_group(a.naik, a.parity, g.Vh, s, grp, u);
 #pragma unroll
-                for (int r = 0; r < R; r++) {
-                    if (act[r]) {
-                        float sc_in = 1.0f;
-                        if (P == HISQ_FP16) sc_in = __ldg(vin.scale + (long)nb * a.n + r0 + r);
+                        for (int l = 0; l < NaikC::G; l++) {
+                            const int slot = grp * NaikC::G + l;
+                            const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -3 : 3);
+                            Cplx<real> M[3][3];
+                            NaikC::decode(u, l, (real)1, M);
+                            Cplx<real> v[R][3];
 #pragma unroll
-                        for (int c = 0; c < 3; c++) v[r][c] = load_elem<P>(vin, ((long)nb * 3 + c) * a.n + r0 + r, sc_in);
-                    } else {
+                            for (int r = 0; r < R; r++) {
+                                if (act[r]) {
+                                    load_vec<P>(vin, nb, r0 + r, v[r]);
+                                } else {
 #pragma unroll
-                        for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+                                    for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+                                }
+                            }
+                            matvec_acc<real, R>(M, v, acc);
+                        }
+                    }
+                    continue;
+                }
+                real lscale = (real)1;
+                if (f.scale) lscale = (real)__ldg(f.scale + (size_t)a.parity * g.Vh + s);
+#pragma unroll
+                for (int grp = 0; grp < FatC::GROUPS; grp++) {
+                    uint32_t u[FatC::WG * 4];
+                    FatC::load_group(f, a.parity, g.Vh, s, grp, u);
+#pragma unroll
+                    for (int l = 0; l < FatC::G; l++) {
+                        const int slot = grp * FatC::G + l;
+                        const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -hop : hop);
+                        Cplx<real> M[3][3];
+                        FatC::decode(u, l, lscale, M);
+                        Cplx<real> v[R][3];
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            if (act[r]) {
+                                load_vec<P>(vin, nb, r0 + r, v[r]);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+                            }
+                        }
+                        matvec_acc<real, R>(M, v, acc);
                     }
                 }
-                matvec_acc<real, R>(M, v, acc);
             }
         }
-        // ---- Naik links: three hops ----
-        real nscale = (real)1;
-        if (NR == 18 && a.naik.scale) nscale = (real)__ldg(a.naik.scale + (size_t)a.parity * g.Vh + s);
+        if constexpr (S == 2) {
+            // add the fat and Naik halves; every lane of the warp takes part
 #pragma unroll
-        for (int grp = 0; grp < NaikC::GROUPS; grp++) {
-            uint32_t u[NaikC::WG * 4];
-            NaikC::load_group(a.naik, a.parity, g.Vh, s, grp, u);
+            for (int r = 0; r < R; r++)
 #pragma unroll
-            for (int l = 0; l < NaikC::G; l++) {
-                const int slot = grp * NaikC::G + l;
-                const int mu = slot >> 1;
-                const int nb = neighbour(g, sc, s, mu, (slot & 1) ? -3 : 3);
-                Cplx<real> M[3][3];
-                NaikC::decode(u, l, nscale, M);
-                Cplx<real> v[R][3];
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    if (act[r]) {
-                        float sc_in = 1.0f;
-                        if (P == HISQ_FP16) sc_in = __ldg(vin.scale + (long)nb * a.n + r0 + r);
-#pragma unroll
-                        for (int c = 0; c < 3; c++) v[r][c] = load_elem<P>(vin, ((long)nb * 3 + c) * a.n + r0 + r, sc_in);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
-                    }
+                for (int c = 0; c < 3; c++) {
+                    acc[r][c].re += __shfl_xor_sync(0xffffffffu, acc[r][c].re, 1);
+                    acc[r][c].im += __shfl_xor_sync(0xffffffffu, acc[r][c].im, 1);
                 }
-                matvec_acc<real, R>(M, v, acc);
-            }
         }
+        if (!valid || part != 0) continue;
 
         // ---- epilogue ----
         if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
             for (int r = 0; r < R; r++)
-                if (act[r]) store_site<P>(vout, s, r0 + r, acc[r]);
+                if (act[r]) store_vec<P>(vout, s, r0 + r, acc[r]);
         } else if constexpr (EPI == EPI_AOP) {
             const VecView<P> vp = view<P>(a.axpy, g.Vh, a.n);
             const real m2 = (real)a.mass2;
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 if (!act[r]) continue;
-                float sc_p = 1.0f;
-                if (P == HISQ_FP16) sc_p = __ldg(vp.scale + (long)s * a.n + r0 + r);
-                Cplx<real> w[3];
+                Cplx<real> p[3], w[3];
+                load_vec<P>(vp, s, r0 + r, p);
                 real d = 0;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    Cplx<real> p = load_elem<P>(vp, ((long)s * 3 + c) * a.n + r0 + r, sc_p);
-                    w[c] = {m2 * p.re - acc[r][c].re, m2 * p.im - acc[r][c].im};
-                    d += p.re * w[c].re + p.im * w[c].im;
+                    w[c] = {m2 * p[c].re - acc[r][c].re, m2 * p[c].im - acc[r][c].im};
+                    d += p[c].re * w[c].re + p[c].im * w[c].im;
                 }
                 dot[r] += (double)d;
-                store_site<P>(vout, s, r0 + r, w);
+                store_vec<P>(vout, s, r0 + r, w);
             }
         } else {
             static_assert(EPI == EPI_RESID && P == HISQ_FP64, "residual epilogue is FP64 only");
@@ -242,16 +297,16 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
                 if (!act[r]) continue;
                 Cplx<double> w[3];
                 double d = 0.0;
+                Cplx<double> x[3], b[3];
+                load_vec<HISQ_FP64>(vx, s, r0 + r, x);
+                load_vec<HISQ_FP64>(vb, s, r0 + r, b);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    long idx = ((long)s * 3 + c) * a.n + r0 + r;
-                    Cplx<double> x = load_elem<HISQ_FP64>(vx, idx, 1.0f);
-                    Cplx<double> b = load_elem<HISQ_FP64>(vb, idx, 1.0f);
-                    w[c] = {b.re - a.mass2 * x.re + (double)acc[r][c].re, b.im - a.mass2 * x.im + (double)acc[r][c].im};
+                    w[c] = {b[c].re - a.mass2 * x[c].re + (double)acc[r][c].re, b[c].im - a.mass2 * x[c].im + (double)acc[r][c].im};
                     d += w[c].re * w[c].re + w[c].im * w[c].im;
                 }
                 dot[r] += d;
-                if (a.out) store_site<HISQ_FP64>(vout, s, r0 + r, w);
+                if (a.out) store_vec<HISQ_FP64>(vout, s, r0 + r, w);
                 if (a.out_lo) {
                     long base = (long)s * 3 * a.n + r0 + r;
                     if (a.lo_prec == HISQ_FP64) {
@@ -277,6 +332,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
             for (int r = 0; r < R; r++)
                 if (r < nvalid) red[sl * a.n + r0 + r] = dot[r];
         }
+        // every thread reaches the reduction (idle threads contributed zeros)
         block_reduce_finish(red, a.spb, a.n, a.n, a.red);
     }
 }

@@ -84,99 +84,86 @@ template <> struct Prec<HISQ_BF16> { using real = float; using store = __nv_bflo
 
 template <typename R> struct Cplx { R re, im; };
 
-// bytes of one complex element of an internal vector
-__host__ __device__ constexpr int vec_elem_bytes(int prec) {
-    return prec == HISQ_FP64 ? 16 : prec == HISQ_FP32 ? 8 : 4;
-}
-
-// offset of the FP16 per-(site, rhs) scale array inside a bundle
-__host__ __device__ inline size_t fp16_scale_offset(int Vh, int n) {
-    size_t main = (size_t)Vh * 3 * n * 4;
-    return (main + 255) & ~(size_t)255;
-}
-
+// Internal vector bundles of n right-hand sides.  FP64, FP32 and BF16: element (s, c, r) is the
+// complex number at (s*3 + c)*n + r (double2 / float2 / bf16x2).  FP16: one 16-byte record per
+// (site, rhs) at s*n + r holding the three colour components as half2 and the FP32 scale
+// (value = half * scale, scale = max |component|), so a neighbour is a single 16-byte load.
 inline size_t vector_bytes(int prec, int Vh, int n) {
-    if (prec == HISQ_FP16) return fp16_scale_offset(Vh, n) + (size_t)Vh * n * 4;
-    return (size_t)Vh * 3 * n * vec_elem_bytes(prec);
+    const size_t elems = (size_t)Vh * n;
+    switch (prec) {
+    case HISQ_FP64: return elems * 3 * 16;
+    case HISQ_FP32: return elems * 3 * 8;
+    case HISQ_FP16: return elems * 16;
+    default: return elems * 3 * 4;
+    }
 }
 
-// A bundle of n right-hand sides in the internal layout, typed by precision.
 template <int P> struct VecView {
     void *data;
-    float *scale;  // FP16 only
     int n;
 };
 
 template <int P>
-__device__ __forceinline__ Cplx<typename Prec<P>::real> load_elem(const VecView<P> &v, long idx, float sc);
-
-template <>
-__device__ __forceinline__ Cplx<double> load_elem<HISQ_FP64>(const VecView<HISQ_FP64> &v, long idx, float) {
-    double2 d = __ldg(reinterpret_cast<const double2 *>(v.data) + idx);
-    return {d.x, d.y};
-}
-template <>
-__device__ __forceinline__ Cplx<float> load_elem<HISQ_FP32>(const VecView<HISQ_FP32> &v, long idx, float) {
-    float2 d = __ldg(reinterpret_cast<const float2 *>(v.data) + idx);
-    return {d.x, d.y};
-}
-template <>
-__device__ __forceinline__ Cplx<float> load_elem<HISQ_FP16>(const VecView<HISQ_FP16> &v, long idx, float sc) {
-    __half2 h = __ldg(reinterpret_cast<const __half2 *>(v.data) + idx);
-    float2 f = __half22float2(h);
-    return {f.x * sc, f.y * sc};
-}
-template <>
-__device__ __forceinline__ Cplx<float> load_elem<HISQ_BF16>(const VecView<HISQ_BF16> &v, long idx, float) {
-    __nv_bfloat162 h = __ldg(reinterpret_cast<const __nv_bfloat162 *>(v.data) + idx);
-    float2 f = __bfloat1622float2(h);
-    return {f.x, f.y};
-}
-
-// load the 3 colours of right-hand sides r0..r0+R-1 at site s
-template <int P, int R>
-__device__ __forceinline__ void load_site(const VecView<P> &v, int s, int r0, int nvalid,
-                                          Cplx<typename Prec<P>::real> out[R][3]) {
+__device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cplx<typename Prec<P>::real> w[3]) {
+    if constexpr (P == HISQ_FP64) {
+        const double2 *d = reinterpret_cast<const double2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        if (r < nvalid) {
-            float sc = 1.0f;
-            if (P == HISQ_FP16) sc = __ldg(v.scale + (long)s * v.n + r0 + r);
+        for (int c = 0; c < 3; c++) {
+            double2 x = __ldg(d + (long)c * v.n);
+            w[c] = {x.x, x.y};
+        }
+    } else if constexpr (P == HISQ_FP32) {
+        const float2 *d = reinterpret_cast<const float2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
-            for (int c = 0; c < 3; c++) out[r][c] = load_elem<P>(v, ((long)s * 3 + c) * v.n + r0 + r, sc);
-        } else {
+        for (int c = 0; c < 3; c++) {
+            float2 x = __ldg(d + (long)c * v.n);
+            w[c] = {x.x, x.y};
+        }
+    } else if constexpr (P == HISQ_FP16) {
+        uint4 q = __ldg(reinterpret_cast<const uint4 *>(v.data) + s * v.n + r);
+        const float sc = __uint_as_float(q.w);
+        const uint32_t h[3] = {q.x, q.y, q.z};
 #pragma unroll
-            for (int c = 0; c < 3; c++) out[r][c] = {0, 0};
+        for (int c = 0; c < 3; c++) {
+            float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&h[c]));
+            w[c] = {f.x * sc, f.y * sc};
+        }
+    } else {
+        const __nv_bfloat162 *d = reinterpret_cast<const __nv_bfloat162 *>(v.data) + s * 3 * v.n + r;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float2 f = __bfloat1622float2(__ldg(d + (long)c * v.n));
+            w[c] = {f.x, f.y};
         }
     }
 }
 
-// store the 3 colours of one right-hand side r at site s (FP16: computes the scale)
 template <int P>
-__device__ __forceinline__ void store_site(const VecView<P> &v, int s, int r,
-                                           const Cplx<typename Prec<P>::real> w[3]) {
-    long base = (long)s * 3 * v.n + r;
+__device__ __forceinline__ void store_vec(const VecView<P> &v, long s, int r, const Cplx<typename Prec<P>::real> w[3]) {
     if constexpr (P == HISQ_FP64) {
-        double2 *d = reinterpret_cast<double2 *>(v.data);
+        double2 *d = reinterpret_cast<double2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
-        for (int c = 0; c < 3; c++) d[base + (long)c * v.n] = make_double2(w[c].re, w[c].im);
+        for (int c = 0; c < 3; c++) d[(long)c * v.n] = make_double2(w[c].re, w[c].im);
     } else if constexpr (P == HISQ_FP32) {
-        float2 *d = reinterpret_cast<float2 *>(v.data);
+        float2 *d = reinterpret_cast<float2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
-        for (int c = 0; c < 3; c++) d[base + (long)c * v.n] = make_float2(w[c].re, w[c].im);
+        for (int c = 0; c < 3; c++) d[(long)c * v.n] = make_float2(w[c].re, w[c].im);
     } else if constexpr (P == HISQ_FP16) {
         float m = 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; c++) m = fmaxf(m, fmaxf(fabsf(w[c].re), fabsf(w[c].im)));
-        float inv = m > 0.0f ? 1.0f / m : 0.0f;
-        __half2 *d = reinterpret_cast<__half2 *>(v.data);
+        const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+        uint32_t h[3];
 #pragma unroll
-        for (int c = 0; c < 3; c++) d[base + (long)c * v.n] = __floats2half2_rn(w[c].re * inv, w[c].im * inv);
-        v.scale[(long)s * v.n + r] = m;
+        for (int c = 0; c < 3; c++) {
+            __half2 x = __floats2half2_rn(w[c].re * inv, w[c].im * inv);
+            h[c] = *reinterpret_cast<uint32_t *>(&x);
+        }
+        reinterpret_cast<uint4 *>(v.data)[s * v.n + r] = make_uint4(h[0], h[1], h[2], __float_as_uint(m));
     } else {
-        __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(v.data);
+        __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
-        for (int c = 0; c < 3; c++) d[base + (long)c * v.n] = __floats2bfloat162_rn(w[c].re, w[c].im);
+        for (int c = 0; c < 3; c++) d[(long)c * v.n] = __floats2bfloat162_rn(w[c].re, w[c].im);
     }
 }
 
@@ -243,6 +230,7 @@ struct TuneKey {
 struct LaunchShape {
     int R;        // right-hand sides per thread
     int threads;  // threads per block
+    int S = 1;    // lanes per (site, rhs group): 2 splits the fat and Naik halves (18-real Naik)
 };
 
 struct Workspace;  // solver workspace (solver.cu)
@@ -256,6 +244,7 @@ struct hisq_ctx {
     int num_sms;
     hisq_solver_params params;
     std::map<hisq::TuneKey, hisq::LaunchShape> tuned;
+    unsigned tune_generation = 0;  // bumped whenever a launch shape changes (captured graphs go stale)
     // generic scratch: reductions (partials + counter) and the A-operator intermediate
     double *partials;       // [max_blocks * HISQ_MAX_NRHS * 2]
     size_t partials_cap;
@@ -277,7 +266,14 @@ hisq_ctx *current();
 int require_ctx(hisq_ctx **ctx);
 int ensure_scratch(hisq_ctx *ctx, size_t partial_doubles, size_t tmp_bytes);
 bool is_device_ptr(const void *p);
-int grid_for(hisq_ctx *ctx, long work_items, int threads, int max_waves = 8);
+// Largest grid <= max_blocks that gives every block the same number of tiles (one fewer for
+// some when tiles is not a multiple), so no SM waits on a straggling extra tile.
+inline long balanced_grid(long tiles, long max_blocks) {
+    if (max_blocks < 1) max_blocks = 1;
+    if (tiles <= max_blocks) return tiles < 1 ? 1 : tiles;
+    long per_block = (tiles + max_blocks - 1) / max_blocks;
+    return (tiles + per_block - 1) / per_block;
+}
 
 // Dslash family launchers (context.cu)
 enum Epilogue { EPI_PLAIN = 0, EPI_AOP = 1, EPI_RESID = 2 };
@@ -300,9 +296,11 @@ struct DslashArgs {
     double *dot_out;       // reduced dots [n]
     int hook;              // solver hook run by the last block (0 = none)
     void *hook_state;
+    int partials_only;     // reducing epilogues: publish per-block partials only (no finish)
 };
+// grid_out (optional) receives the number of blocks launched (= partials written per dot)
 int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, bool use64,
-                  const DslashArgs &a, const LaunchShape *shape, cudaStream_t stream);
+                  const DslashArgs &a, const LaunchShape *shape, cudaStream_t stream, int *grid_out = nullptr);
 LaunchShape default_shape(int prec, int n);
 LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64);
 void free_workspace(hisq_ctx *ctx);  // solver.cu

@@ -262,6 +262,7 @@ static RedArgs red_of(PcWork &w, double *dot_out) {
     r.dot_out = dot_out;
     r.hook = 0;
     r.st = nullptr;
+    r.partials_only = 0;
     return r;
 }
 
@@ -323,8 +324,8 @@ static int backward(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const his
 }
 
 static int reduce_launch(hisq_ctx *ctx, void (*k)(LossArgs), LossArgs a, cudaStream_t st) {
-    int threads = a.spb * a.K;  // rows of the block reduction (spb) must be a power of two
-    size_t smem = threads * sizeof(double);
+    int threads = (a.spb * a.K + 31) / 32 * 32;  // whole warps; rows beyond spb idle
+    size_t smem = (threads + 64) * sizeof(double);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     long tiles = (a.Vh + a.spb - 1) / a.spb;

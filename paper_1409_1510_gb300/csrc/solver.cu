@@ -29,19 +29,13 @@ struct BlasArgs {
     RedArgs red;
     SolverState *st;
     const int *gate;
+    const double *alpha_partials;  // plain CG: per-block <p, A p> partials of the A-operator
+    int alpha_nblk;                // kernel (summed by every block of the update kernel)
 };
 
 template <int P>
-__device__ __forceinline__ float site_scale(const VecView<P> &v, int s, int r) {
-    if constexpr (P == HISQ_FP16) return v.scale[(long)s * v.n + r];
-    return 1.0f;
-}
-
-template <int P>
 __device__ __forceinline__ void load3(const VecView<P> &v, int s, int r, Cplx<typename Prec<P>::real> w[3]) {
-    float sc = site_scale<P>(v, s, r);
-#pragma unroll
-    for (int c = 0; c < 3; c++) w[c] = load_elem<P>(v, ((long)s * 3 + c) * v.n + r, sc);
+    load_vec<P>(v, s, r, w);
 }
 
 // one thread per (site, rhs); red rows = sites per block
@@ -77,10 +71,10 @@ __global__ void __launch_bounds__(256) cg_init_kernel(BlasArgs a) {
             bq[c] = {(rq)b[c].re, (rq)b[c].im};
             bp[c] = {(typename Prec<P>::real)b[c].re, (typename Prec<P>::real)b[c].im};
         }
-        store_site<HISQ_FP64>(vxh, s, r, zero);
-        store_site<Q>(vx, s, r, zq);
-        store_site<Q>(vr, s, r, bq);
-        store_site<P>(vp, s, r, bp);
+        store_vec<HISQ_FP64>(vxh, s, r, zero);
+        store_vec<Q>(vx, s, r, zq);
+        store_vec<Q>(vr, s, r, bq);
+        store_vec<P>(vp, s, r, bp);
     }
     const int rows = blockDim.x / a.n;
     for (int i = tid; i < rows * a.n; i += blockDim.x) red[i] = 0.0;
@@ -89,19 +83,64 @@ __global__ void __launch_bounds__(256) cg_init_kernel(BlasArgs a) {
     block_reduce_finish(red, rows, a.n, a.n, a.red);
 }
 
+// Every block sums the A-operator kernel's per-block partials of <p, A p> in the same fixed order,
+// so all blocks hold the identical alpha = |r|^2 / <p, A p> without waiting for one another.
+// Writes alpha and the breakdown mask into shared memory (s_al, s_ok); red is scratch.
+__device__ __forceinline__ void alpha_from_partials(const BlasArgs &a, double *red, double *s_al, int *s_ok) {
+    const int tid = threadIdx.x, n = a.n;
+    int np2 = 1;
+    while (np2 < n) np2 *= 2;
+    const int per = blockDim.x / np2, j = tid % np2, k = tid / np2;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    double s = 0.0;
+    if (j < n && k < per) {
+#pragma unroll 4
+        for (int b = k; b < a.alpha_nblk; b += per) s += __ldcg(a.alpha_partials + (size_t)b * n + j);
+    }
+    for (int off = 16; off >= np2; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const int groups = np2 < 32 ? nwarps : per;
+    if (np2 < 32) {
+        if (lane < np2) red[warp * np2 + lane] = s;
+    } else {
+        red[tid] = s;
+    }
+    __syncthreads();
+    if (tid < n) {
+        double pap = 0.0;
+        for (int q = 0; q < groups; q++) pap += red[q * np2 + tid];
+        const bool ok = pap > 0.0 && isfinite(pap);
+        const double al = ok ? a.st->rr[tid] / pap : 0.0;
+        s_ok[tid] = ok;
+        s_al[tid] = al;
+        if (blockIdx.x == 0) {  // record alpha and a breakdown for the host and the decision step
+            a.st->alpha[tid][0] = al;
+            a.st->alpha[tid][1] = 0.0;
+            if (!ok && a.st->active[tid]) {
+                a.st->active[tid] = 0;
+                a.st->status[tid] = RHS_BREAKDOWN;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // x_lo += alpha p; r_lo -= alpha Ap; |r|^2 -> HOOK_DECIDE   (alpha complex for flexible CG)
 template <int P>
 __global__ void __launch_bounds__(256) cg_update_kernel(BlasArgs a) {
     constexpr int Q = q_prec(P);
     using rq = typename Prec<Q>::real;
     extern __shared__ double red[];
+    __shared__ double s_al[HISQ_MAX_BUNDLE];
+    __shared__ int s_ok[HISQ_MAX_BUNDLE];
     BLAS_PROLOGUE
+    if (a.alpha_partials) alpha_from_partials(a, red, s_al, s_ok);
     auto vx = view<Q>(a.x, a.Vh, a.n);
     auto vr = view<Q>(a.r, a.Vh, a.n);
     auto vp = view<P>(a.p, a.Vh, a.n);
     auto vap = view<P>(a.Ap, a.Vh, a.n);
-    const bool act = a.st->active[r] != 0;
-    const rq al_re = (rq)a.st->alpha[r][0], al_im = (rq)a.st->alpha[r][1];
+    const bool act = a.st->active[r] != 0 && (a.alpha_partials == nullptr || s_ok[r]);
+    const rq al_re = a.alpha_partials ? (rq)s_al[r] : (rq)a.st->alpha[r][0];
+    const rq al_im = a.alpha_partials ? (rq)0 : (rq)a.st->alpha[r][1];
     double acc = 0.0;
     if (act) {
         for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
@@ -123,8 +162,8 @@ __global__ void __launch_bounds__(256) cg_update_kernel(BlasArgs a) {
                 part += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
             }
             acc += (double)part;
-            store_site<Q>(vx, s, r, x);
-            store_site<Q>(vr, s, r, rv);
+            store_vec<Q>(vx, s, r, x);
+            store_vec<Q>(vr, s, r, rv);
         }
     }
     const int rows = blockDim.x / a.n;
@@ -134,31 +173,28 @@ __global__ void __launch_bounds__(256) cg_update_kernel(BlasArgs a) {
     block_reduce_finish(red, rows, a.n, a.n, a.red);
 }
 
-// p = r + beta p for active right-hand sides (plain CG) -> HOOK_LOOP
+// p = r + beta p for active right-hand sides (plain CG); a pure streaming kernel
 template <int P>
 __global__ void __launch_bounds__(256) cg_pupdate_kernel(BlasArgs a) {
     constexpr int Q = q_prec(P);
     using rp = typename Prec<P>::real;
-    extern __shared__ double red[];
     BLAS_PROLOGUE
+    (void)tid;
+    if (!a.st->active[r]) return;
     auto vr = view<Q>(a.r, a.Vh, a.n);
     auto vp = view<P>(a.p, a.Vh, a.n);
-    const bool act = a.st->active[r] != 0;
     const rp be = (rp)a.st->beta[r][0];
-    if (act) {
-        for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
-            int s = tile * a.spb + sl;
-            if (s >= a.Vh || sl >= a.spb) continue;
-            Cplx<typename Prec<Q>::real> rv[3];
-            Cplx<rp> p[3];
-            load3<Q>(vr, s, r, rv);
-            load3<P>(vp, s, r, p);
+    for (int tile = blockIdx.x; (long)tile * a.spb < a.Vh; tile += gridDim.x) {
+        int s = tile * a.spb + sl;
+        if (s >= a.Vh || sl >= a.spb) continue;
+        Cplx<typename Prec<Q>::real> rv[3];
+        Cplx<rp> p[3];
+        load3<Q>(vr, s, r, rv);
+        load3<P>(vp, s, r, p);
 #pragma unroll
-            for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
-            store_site<P>(vp, s, r, p);
-        }
+        for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
+        store_vec<P>(vp, s, r, p);
     }
-    block_reduce_finish(red, 1, 0, a.n, a.red);
 }
 
 // reliable update, first step: x_hi += x_lo; x_lo = 0 for right-hand sides flagged for update
@@ -180,8 +216,8 @@ __global__ void __launch_bounds__(256) cg_xhi_kernel(BlasArgs a) {
         Cplx<typename Prec<Q>::real> zero[3] = {{0, 0}, {0, 0}, {0, 0}};
 #pragma unroll
         for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
-        store_site<HISQ_FP64>(vxh, s, r, xh);
-        store_site<Q>(vx, s, r, zero);
+        store_vec<HISQ_FP64>(vxh, s, r, xh);
+        store_vec<Q>(vx, s, r, zero);
     }
 }
 
@@ -273,8 +309,8 @@ __global__ void __launch_bounds__(256) fcg_pupdate_kernel(BlasArgs a) {
             }
             acc_re += (double)pre;
             acc_im += (double)pim;
-            store_site<P>(vp, s, r, p);
-            store_site<Q>(vro, s, r, rv);
+            store_vec<P>(vp, s, r, p);
+            store_vec<Q>(vro, s, r, rv);
         }
     }
     const int rows = blockDim.x / a.n;
@@ -287,11 +323,6 @@ __global__ void __launch_bounds__(256) fcg_pupdate_kernel(BlasArgs a) {
     block_reduce_finish(red, rows, 2 * a.n, a.n, a.red);
 }
 
-// single block: runs the end-of-iteration hook
-__global__ void loop_hook_kernel(RedArgs ra, int n) {
-    __shared__ double red[32];
-    block_reduce_finish(red, 1, 0, n, ra);
-}
 
 // ------------------------------------------------------------------------------------------
 // Workspace
@@ -303,6 +334,7 @@ struct GraphCache {
     const hisq_pc *pc = nullptr;
     double mass = 0;
     int n = 0, prec = -1;
+    unsigned tune_generation = 0;
 };
 
 struct Workspace {
@@ -315,6 +347,8 @@ struct Workspace {
     SolverState *h_st = nullptr;  // pinned host mirror
     double *partials = nullptr;
     size_t partials_cap = 0;
+    double *partials2 = nullptr;   // the A-operator's <p, A p> partials (summed by the update kernel)
+    int d2_grid = 0;               // blocks of the last A-operator launch enqueued
     unsigned int *counter = nullptr;
     double *dots = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -346,6 +380,7 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
         if (cudaMalloc(&w->st, sizeof(SolverState)) != cudaSuccess ||
             cudaMallocHost(&w->h_st, sizeof(SolverState)) != cudaSuccess ||
             cudaMalloc(&w->partials, pcap * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&w->partials2, pcap * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&w->counter, sizeof(unsigned int) * 4) != cudaSuccess ||
             cudaMalloc(&w->dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) != cudaSuccess)
             return set_error(HISQ_ERR_NOMEM, "solver workspace allocation failed");
@@ -393,6 +428,7 @@ void free_workspace(hisq_ctx *ctx) {
     if (w->st) cudaFree(w->st);
     if (w->h_st) cudaFreeHost(w->h_st);
     if (w->partials) cudaFree(w->partials);
+    if (w->partials2) cudaFree(w->partials2);
     if (w->counter) cudaFree(w->counter);
     if (w->dots) cudaFree(w->dots);
     if (w->ev0) cudaEventDestroy(w->ev0);
@@ -444,12 +480,12 @@ static BlasArgs blas_args(const Solve &S) {
 
 template <typename K>
 static int launch_blas(const Solve &S, K kernel, BlasArgs a, int hook, bool reduce) {
-    int threads = a.spb * a.n;
-    size_t smem = reduce ? (size_t)std::max(threads, a.spb * a.n * 2) * sizeof(double) : 0;
+    int threads = (a.spb * a.n + 31) / 32 * 32;  // whole warps; rows beyond spb idle
+    size_t smem = reduce ? (size_t)(2 * threads + 64) * sizeof(double) : 0;  // red[rows][2n] and the final sums
     long tiles = (a.Vh + a.spb - 1) / a.spb;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    long grid = std::min<long>(tiles, (long)std::max(per_sm, 1) * S.ctx->num_sms);
+    long grid = balanced_grid(tiles, (long)std::min(std::max(per_sm, 1), 4) * S.ctx->num_sms);
     if ((size_t)grid * a.n * 2 > S.w->partials_cap) grid = S.w->partials_cap / (a.n * 2);
     a.red.hook = hook;
     kernel<<<(int)grid, threads, smem, S.st>>>(a);
@@ -462,8 +498,13 @@ static int enqueue_blas(const Solve &S, int which) {
     BlasArgs a = blas_args(S);
     switch (which) {
     case HOOK_INIT: return launch_blas(S, cg_init_kernel<P>, a, HOOK_INIT, true);
-    case HOOK_DECIDE: return launch_blas(S, cg_update_kernel<P>, a, HOOK_DECIDE, true);
-    case HOOK_LOOP: return launch_blas(S, cg_pupdate_kernel<P>, a, HOOK_LOOP, true);
+    case HOOK_DECIDE:
+        if (!S.pc) {  // plain CG: alpha from the A-operator's partials, summed in every block
+            a.alpha_partials = S.w->partials2;
+            a.alpha_nblk = S.w->d2_grid;
+        }
+        return launch_blas(S, cg_update_kernel<P>, a, HOOK_DECIDE, true);
+    case HOOK_LOOP: return launch_blas(S, cg_pupdate_kernel<P>, a, HOOK_NONE, false);
     case HOOK_FCG_BETA: return launch_blas(S, fcg_beta_kernel<P>, a, HOOK_FCG_BETA, true);
     case HOOK_FCG_PR: return launch_blas(S, fcg_pupdate_kernel<P>, a, HOOK_FCG_PR, true);
     default: {
@@ -482,8 +523,8 @@ static int blas(const Solve &S, int which) {
     }
 }
 
-static int dslash_step(const Solve &S, DslashArgs d, bool use64) {
-    d.partials = S.w->partials;
+static int dslash_step(const Solve &S, DslashArgs d, bool use64, int *grid_out = nullptr) {
+    if (!d.partials_only) d.partials = S.w->partials;
     d.partials_cap = S.w->partials_cap;
     d.counter = S.w->counter;
     d.dot_out = S.w->dots;
@@ -494,7 +535,7 @@ static int dslash_step(const Solve &S, DslashArgs d, bool use64) {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, S.st);
     }
-    int rc = launch_dslash(S.ctx, S.fat, S.naik, use64, d, nullptr, S.st);
+    int rc = launch_dslash(S.ctx, S.fat, S.naik, use64, d, nullptr, S.st, grid_out);
     if (S.timing) {
         cudaEventRecord(e1, S.st);
         (use64 ? S.events64 : S.events)->push_back({e0, e1});
@@ -547,8 +588,16 @@ static int enqueue_iteration_head(const Solve &S) {
     d.epi = EPI_AOP;
     d.mass2 = S.mass * S.mass;
     d.axpy_in = S.w->p;
-    d.hook = S.pc ? HOOK_FCG_ALPHA : HOOK_ALPHA;
-    HISQ_CHECK(dslash_step(S, d, sloppy64));
+    if (S.pc) {
+        d.hook = HOOK_FCG_ALPHA;
+        HISQ_CHECK(dslash_step(S, d, sloppy64));
+    } else {
+        // plain CG: publish <p, A p> per block; the update kernel finishes the sum
+        d.hook = HOOK_NONE;
+        d.partials_only = 1;
+        d.partials = S.w->partials2;
+        HISQ_CHECK(dslash_step(S, d, sloppy64, &S.w->d2_grid));
+    }
     return blas(S, HOOK_DECIDE);
 }
 
@@ -565,14 +614,7 @@ static int enqueue_head(const Solve &S) { return S.pc ? enqueue_fcg_head(S) : en
 // end of an iteration: plain CG updates p here; flexible CG only advances the loop
 static int enqueue_tail(const Solve &S) {
     if (!S.pc) return blas(S, HOOK_LOOP);
-    RedArgs ra;
-    memset(&ra, 0, sizeof(ra));
-    ra.counter = S.w->counter;
-    ra.hook = HOOK_LOOP;
-    ra.st = S.w->st;
-    loop_hook_kernel<<<1, 32, 0, S.st>>>(ra, S.n);
-    HISQ_CUDA(cudaGetLastError());
-    return HISQ_OK;
+    return HISQ_OK;  // flexible CG builds its direction at the start of the next iteration
 }
 
 static int enqueue_setup(const Solve &S) {
@@ -595,6 +637,8 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->delta = P.delta;
     h->h_loop = h_loop;
     h->h_upd = h_upd;
+    h->cond_loop = 1;  // the defaults the graph assigns at launch
+    h->cond_upd = 0;
     HISQ_CUDA(cudaMemcpyAsync(S.w->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, S.st));
     return HISQ_OK;
 }
@@ -682,6 +726,7 @@ static int build_graph(const Solve &S) {
     w->gc.n = S.n;
     w->gc.prec = S.prec;
     w->gc.pc = S.pc;
+    w->gc.tune_generation = S.ctx->tune_generation;
     return HISQ_OK;
 }
 
@@ -694,7 +739,8 @@ static int solve_bundle(Solve &S, double tol) {
     bool graph = P.use_graph && !S.timing;
     if (graph) {
         bool reuse = w->gc.exec && w->gc.fat == S.fat && w->gc.naik == S.naik && w->gc.mass == S.mass &&
-                     w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == S.pc;
+                     w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == S.pc &&
+                     w->gc.tune_generation == S.ctx->tune_generation;
         unsigned long long hl = w->h_st->h_loop, hu = w->h_st->h_upd;
         if (!reuse) {
             HISQ_CHECK(build_graph(S));
@@ -829,7 +875,7 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
         // p-update; the three residual-recomputation kernels run when an update is due (graph)
         // or are launched every iteration as gated no-ops (host-driven)
         bool graph_mode = P.use_graph && !S.timing;
-        long per_iter = P.pc ? 4 + 5 + 3 : 4;  // flexible CG adds 5 network layers, beta and loop kernels
+        long per_iter = P.pc ? 3 + 5 + 2 : 4;  // flexible CG: 5 network layers, beta and direction kernels
         stats.kernel_launches += 3 + per_iter * h.bundle_iters + 3L * (graph_mode ? h.update_rounds : h.bundle_iters);
         stats.bundle_iterations += bmax;
         stats.bundles++;

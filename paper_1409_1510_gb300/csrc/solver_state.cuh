@@ -13,7 +13,7 @@ enum Hook {
     HOOK_ALPHA = 2,     // dots = <p, A p>: alpha = rr / pAp          (plain CG)
     HOOK_DECIDE = 3,    // dots = |r|^2 after the update: beta or reliable update
     HOOK_RELIABLE = 4,  // dots = |b - A x_hi|^2 (FP64): convergence, restart of r
-    HOOK_LOOP = 5,      // no dots: advance the iteration counter, set the loop condition
+    HOOK_LOOP = 5,      // (unused: HOOK_DECIDE and HOOK_RELIABLE set the loop condition)
     HOOK_FCG_ALPHA = 6, // dots = <p, A p>; with <p, r> from HOOK_FCG_PR: alpha for flexible CG
     HOOK_FCG_BETA = 7,  // dots = <r - r_old, z> (complex): beta for flexible CG
     HOOK_FCG_PR = 8,    // dots = <p, r> (complex) of the new direction
@@ -53,10 +53,19 @@ struct SolverState {
     double delta;
     unsigned long long h_loop;        // conditional handles (0 when not in a graph)
     unsigned long long h_upd;
+    int cond_loop;                    // last value given to each handle (the graph assigns the
+    int cond_upd;                     // defaults 1 and 0 at every launch)
+    int pad_;
 };
+static_assert(sizeof(SolverState) % sizeof(uint32_t) == 0, "the state is copied as 32-bit words");
 
-__device__ __forceinline__ void set_condition(unsigned long long handle, unsigned int value) {
-    if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, value);
+// Sets a graph condition only when its value changes (the call is not free and most iterations
+// leave both conditions as they are).
+__device__ __forceinline__ void set_condition(unsigned long long handle, int *last, unsigned int value) {
+    if (handle && (unsigned int)*last != value) {
+        cudaGraphSetConditional((cudaGraphConditionalHandle)handle, value);
+        *last = (int)value;
+    }
 }
 
 // Scalar step of the solver for one bundle.  Called by thread 0 of the last block of a reducing
@@ -198,7 +207,14 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
         }
         st->any_update = any;
         st->update_rounds += any;
-        set_condition(st->h_upd, any);
+        set_condition(st->h_upd, &st->cond_upd, any);
+        // end of the iteration's scalar work: count it and decide whether the loop continues
+        // (right-hand sides flagged for an update stay active until HOOK_RELIABLE decides)
+        int act = 0;
+        for (int k = 0; k < n; k++) act |= st->active[k];
+        st->any_active = act;
+        st->bundle_iters += 1;
+        set_condition(st->h_loop, &st->cond_loop, (act && st->bundle_iters < st->max_iter) ? 1u : 0u);
         break;
     }
     case HOOK_RELIABLE: {
@@ -228,18 +244,10 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
                 st->r_upd[k] = rn;
             }
         }
-        break;
-    }
-    case HOOK_LOOP: {
-        int any = 0;
-        for (int k = 0; k < n; k++) {
-            st->update[k] = 0;
-            any |= st->active[k];
-        }
-        st->any_active = any;
-        st->any_update = 0;
-        st->bundle_iters += 1;
-        set_condition(st->h_loop, (any && st->bundle_iters < st->max_iter) ? 1u : 0u);
+        int act = 0;
+        for (int k = 0; k < n; k++) act |= st->active[k];
+        st->any_active = act;
+        set_condition(st->h_loop, &st->cond_loop, (act && st->bundle_iters < st->max_iter) ? 1u : 0u);
         break;
     }
     default:

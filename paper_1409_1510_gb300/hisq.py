@@ -72,8 +72,8 @@ _SIGNATURES = {
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_cg_solve": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _D, _D], _I),
     "hisq_last_stats": ([ctypes.POINTER(hisq_solve_stats), _VP, _VP], _I),
-    "hisq_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
-    "hisq_set_launch_shape": ([_I, _I, _I, _I, _I], _I),
+    "hisq_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "hisq_set_launch_shape": ([_I, _I, _I, _I, _I, _I], _I),
     "hisq_pc_create": ([ctypes.POINTER(_VP), _VP], _I),
     "hisq_pc_destroy": ([_VP], _I),
     "hisq_pc_set_weights": ([_VP, _VP], _I),
@@ -216,13 +216,16 @@ def hisq_last_stats(iterations=None, true_residual=None) -> hisq_solve_stats:
 
 
 def hisq_autotune(fat, naik, nrhs: int):
-    r, t = _I(), _I()
-    _check(load().hisq_autotune(fat, naik, int(nrhs), ctypes.byref(r), ctypes.byref(t)))
-    return r.value, t.value
+    """Returns (rhs_per_thread, block_threads, lanes_per_site) of the fastest shape."""
+    r, t, s = _I(), _I(), _I()
+    _check(load().hisq_autotune(fat, naik, int(nrhs), ctypes.byref(r), ctypes.byref(t), ctypes.byref(s)))
+    return r.value, t.value, s.value
 
 
-def hisq_set_launch_shape(prec: int, recon: int, nrhs: int, rhs_per_thread: int, block_threads: int):
-    _check(load().hisq_set_launch_shape(int(prec), int(recon), int(nrhs), int(rhs_per_thread), int(block_threads)))
+def hisq_set_launch_shape(prec: int, recon: int, nrhs: int, rhs_per_thread: int, block_threads: int,
+                          lanes_per_site: int = 1):
+    _check(load().hisq_set_launch_shape(int(prec), int(recon), int(nrhs), int(rhs_per_thread), int(block_threads),
+                                        int(lanes_per_site)))
 
 
 def hisq_pc_create(weights=None):

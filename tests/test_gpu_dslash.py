@@ -41,11 +41,32 @@ def test_every_launch_shape(prec):
         for R in (1, 2, 4, 8):
             if prec == 0 and R == 8:
                 continue
-            for threads in (32, 96, 256):
-                g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads)
-                vout.zero_()
-                g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 1)
-                assert rel_err(g.unpack(vout, n), want) <= PREC_TOL[prec], (R, threads)
+            for S in (1, 2):
+                if S == 2 and R == 8:
+                    continue
+                for threads in (32, 96, 256):
+                    g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads, S)
+                    vout.zero_()
+                    g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 1)
+                    assert rel_err(g.unpack(vout, n), want) <= PREC_TOL[prec], (R, S, threads)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 3])
+def test_lane_split_with_fused_epilogues(prec, n):
+    """The two-lane (fat / Naik) split with the A-operator epilogue and its fused dot."""
+    mass = 0.2
+    with gpu(DIMS, prec, 18) as g:
+        v = _rhs(g.lat, n, 80)
+        for S in (1, 2):
+            g.hisq.hisq_set_launch_shape(prec, 18, n, 1, 128, S)
+            vin, vout = g.pack(v), g.bundle(n)
+            pap = np.zeros(n)
+            g.hisq.hisq_aop(g.fat, g.naik, mass, vin, vout, n, pap)
+            assert rel_err(g.unpack(vout, n), g.oracle.aop(v, mass)) <= 2 * PREC_TOL[prec], S
+            vq = g.unpack(vin, n)
+            want_dot = np.array([np.vdot(vq[k], g.oracle.aop(vq[k], mass)).real for k in range(n)])
+            assert np.max(np.abs(pap - want_dot) / np.abs(want_dot)) <= 4 * PREC_TOL[prec], S
 
 
 def test_dslash_max_nrhs_and_single_site_row():
