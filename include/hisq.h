@@ -160,14 +160,20 @@ typedef struct {
     double delta;         /* reliable update when |r| < delta * |r at the last update| (0.1) */
     int max_iter;         /* per right-hand side (default 20000) */
     int bundle;           /* right-hand sides per bundle, 1..HISQ_MAX_BUNDLE; 0 = autotuned */
-    int use_graph;        /* 1: whole solve as one captured CUDA graph with device-side
-                             control flow; 0: host-driven iterations */
+    int use_graph;        /* driver of a bundle: 0 host-driven iterations; 1 one captured CUDA
+                             graph with device-side control flow (WHILE/IF conditional nodes);
+                             2 (default) one persistent cooperative kernel for the whole solve,
+                             with bounded grid barriers (plain CG, 18-real Naik links; otherwise,
+                             or if the grid cannot be co-resident, the graph driver) */
     int check_every;      /* host-driven mode: iterations between residual read-backs (1) */
     const hisq_pc *pc;    /* learned preconditioner for flexible CG; NULL = plain CG */
     int stall_window;     /* flexible CG: fall back to plain CG if the residual does not drop */
     double stall_factor;  /* by stall_factor within stall_window iterations (10, 50) */
     int autotune;         /* 1: time the Dslash launch shapes on first use of a shape */
     int time_kernels;     /* 1: record CUDA events around every Dslash launch (stats) */
+    int debug_barrier_timeout; /* test hook for failure detection: 1 makes every grid barrier of
+                             the persistent solve wait for one block more than it launches, so the
+                             bounded waits run out and the solve returns HISQ_ERR_TIMEOUT */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);
@@ -239,6 +245,12 @@ int hisq_pc_get_weights(const hisq_pc *pc, double *weights /* host */);
 /* out = M(in) for nrhs (1..HISQ_MAX_BUNDLE) FP32 internal even-site vectors (device). */
 int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
                   const void *in, void *out, int nrhs);
+
+/* out = M_H(in), M_H = (M + M^dag) / 2 the Hermitian part of the network (M^dag applies the adjoint
+ * layers in reverse order).  This is the preconditioner hisq_cg_solve applies in flexible CG: a
+ * trained M is not Hermitian, and its Hermitian part keeps the short CG recurrence valid. */
+int hisq_pc_apply_hermitian(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                            const void *in, void *out, int nrhs);
 
 /* Training loss over K pairs (r_k, e_k) with A e_k = r_k (residual and error of a CG iterate):
  *   loss = (1/K) sum_k |A (M r_k - e_k)|^2 / |r_k|^2,  A = mass^2 - D_eo D_oe,

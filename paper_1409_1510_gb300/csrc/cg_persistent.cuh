@@ -1,0 +1,206 @@
+// The whole mixed-precision CG solve of one bundle as one cooperative, persistent kernel.
+//
+// Every phase of an iteration -- t = D_oe p, A p = m^2 p - D_eo t with <p, A p>, the update of x and
+// r with |r|^2, the decision step, the FP64 residual recomputation when one is due, and p = r + beta p
+// -- runs inside one launch, separated by grid barriers.  Each block keeps its own shared-memory copy
+// of the bundle state and evolves it identically: after a barrier every block sums the same
+// per-block partials in the same order and runs the same scalar step, so nothing has to be
+// broadcast.  The barrier is a generation counter whose wait is bounded: a block that waits longer
+// than the spin limit sets an error flag and the whole grid returns (HISQ_ERR_TIMEOUT on the host).
+// Vectors written inside the launch are read with ld.global.cg (L2), never the read-only path.
+#pragma once
+#include "dslash_kernel.cuh"
+
+namespace hisq {
+
+struct PersArgs {
+    Geom g;
+    LinkField fat, naik;      // inner precision (18-real Naik)
+    LinkField fat64, naik64;  // FP64 copies
+    void *p, *t, *ap;         // inner precision bundles
+    void *x, *r;              // x_lo and r in the iterated precision
+    void *b, *xhi, *t64;      // FP64
+    double mass2;
+    int n;
+    double *partials;         // [gridDim][PERS_ND]
+    SolverState *st;          // initial state in, final state out (block 0)
+    unsigned int *bar;        // [0] arrivals, [1] generation
+    int *err;
+    long long spin_limit;
+    unsigned int expected;    // arrivals that complete a barrier (gridDim.x; more only to test timeouts)
+};
+
+constexpr int PERS_ND = 2 * HISQ_MAX_BUNDLE;
+
+__device__ __forceinline__ bool grid_sync(const PersArgs &a) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*reinterpret_cast<volatile int *>(a.err) != 0) {  // the grid is already giving up
+            s_ok = 0;
+        } else {
+        volatile unsigned int *gen = a.bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        if (atomicAdd(a.bar, 1u) == a.expected - 1) {
+            a.bar[0] = 0u;
+            __threadfence();
+            atomicAdd(a.bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > a.spin_limit) {
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = *reinterpret_cast<volatile int *>(a.err) == 0;
+        }
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+// per-block column sums of red[rows][ndots] into partials[blockIdx.x][*]
+__device__ __forceinline__ void block_partials(const PersArgs &a, double *red, int rows, int ndots) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    __syncthreads();
+    for (int j = warp; j < ndots; j += nwarps) {
+        double s = 0.0;
+        for (int row = lane; row < rows; row += 32) s += red[row * ndots + j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+    }
+}
+
+// every block: dots[j] = sum over blocks of partials[b][j], j < ndots, in a fixed order
+__device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int ndots, double *dots) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    int np2 = 1;
+    while (np2 < ndots) np2 *= 2;
+    const int per = blockDim.x / np2, j = tid % np2, k = tid / np2;
+    double s = 0.0;
+    if (j < ndots && k < per) {
+#pragma unroll 4
+        for (int b = k; b < (int)gridDim.x; b += per) s += __ldcg(a.partials + (size_t)b * PERS_ND + j);
+    }
+    for (int off = 16; off >= np2; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const int groups = np2 < 32 ? nwarps : per;
+    __syncthreads();
+    if (np2 < 32) {
+        if (lane < np2) red[warp * np2 + lane] = s;
+    } else {
+        red[tid] = s;
+    }
+    __syncthreads();
+    if (tid < ndots) {
+        double t = 0.0;
+        for (int q = 0; q < groups; q++) t += red[q * np2 + tid];
+        dots[tid] = t;
+    }
+    __syncthreads();
+}
+
+// One Dslash phase over all sites of output parity `parity`.  EPI_PLAIN: out = D in;
+// EPI_AOP: out = m^2 axpy - D in with Re<axpy, out> per block; EPI_RESID (FP64): r = b - m^2 x + D in,
+// written to out_lo (iterated precision Q) with |r|^2 per block.  mask[r] selects right-hand sides.
+template <int PP, int R, int EPI, int Q>
+__device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
+                                             const void *in, void *out, int parity, const int *mask,
+                                             const void *axpy, const void *bvec, void *out_lo, double *red) {
+    using real = typename Prec<PP>::real;
+    const Geom &g = a.g;
+    const int n = a.n, t = n / R, spb = blockDim.x / t;
+    const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = gi * R;
+    const VecView<PP> vin{const_cast<void *>(in), n};
+    const VecView<PP> vout{out, n};
+    bool act[R];
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        act[r] = r0 + r < n && mask[r0 + r] != 0;
+        any |= act[r];
+    }
+    double dot[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) dot[r] = 0.0;
+    for (int tile = blockIdx.x; (long)tile * spb < g.Vh; tile += gridDim.x) {
+        const int s = tile * spb + sl;
+        if (sl >= spb || s >= g.Vh || !any) continue;
+        Cplx<real> acc[R][3];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
+        site_stencil<PP, 18, R, 1, true>(g, fat, naik, parity, vin, s, 0, r0, act, acc);
+        if constexpr (EPI == EPI_PLAIN) {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (act[r]) store_vec<PP>(vout, s, r0 + r, acc[r]);
+        } else if constexpr (EPI == EPI_AOP) {
+            const VecView<PP> vp{const_cast<void *>(axpy), n};
+            const real m2 = (real)a.mass2;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                if (!act[r]) continue;
+                Cplx<real> p[3], w[3];
+                load_vec<PP, true>(vp, s, r0 + r, p);
+                real d = 0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    w[c] = {m2 * p[c].re - acc[r][c].re, m2 * p[c].im - acc[r][c].im};
+                    d += p[c].re * w[c].re + p[c].im * w[c].im;
+                }
+                dot[r] += (double)d;
+                store_vec<PP>(vout, s, r0 + r, w);
+            }
+        } else {
+            static_assert(EPI == EPI_RESID && PP == HISQ_FP64, "residual epilogue is FP64");
+            const VecView<HISQ_FP64> vx{const_cast<void *>(axpy), n}, vb{const_cast<void *>(bvec), n};
+            const VecView<Q> vlo{out_lo, n};
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                if (!act[r]) continue;
+                Cplx<double> x[3], b[3];
+                Cplx<typename Prec<Q>::real> lo[3];
+                load_vec<HISQ_FP64, true>(vx, s, r0 + r, x);
+                load_vec<HISQ_FP64, true>(vb, s, r0 + r, b);
+                double d = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    double wr = b[c].re - a.mass2 * x[c].re + (double)acc[r][c].re;
+                    double wi = b[c].im - a.mass2 * x[c].im + (double)acc[r][c].im;
+                    d += wr * wr + wi * wi;
+                    lo[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+                }
+                dot[r] += d;
+                store_vec<Q>(vlo, s, r0 + r, lo);
+            }
+        }
+    }
+    if constexpr (EPI != EPI_PLAIN) {
+        for (int i = tid; i < spb * n; i += blockDim.x) red[i] = 0.0;
+        __syncthreads();
+        if (sl < spb) {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (r0 + r < n) red[sl * n + r0 + r] = dot[r];
+        }
+        block_partials(a, red, spb, n);
+    }
+}
+
+// the solve loop (body in cg_persistent_body.cuh, instantiated per precision)
+template <int P, int R>
+__global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(PersArgs a);
+
+template <int P>
+cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, size_t smem, cudaStream_t st);
+template <int P>
+cudaError_t persistent_occupancy(int R, size_t smem, int *blocks_per_sm);
+
+}  // namespace hisq

@@ -417,7 +417,7 @@ void hisq_default_solver_params(hisq_solver_params *p) {
     p->delta = 0.1;
     p->max_iter = 20000;
     p->bundle = 0;
-    p->use_graph = 1;
+    p->use_graph = 2;
     p->check_every = 1;
     p->pc = nullptr;
     p->stall_window = 50;

@@ -149,6 +149,80 @@ __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int n
     }
 }
 
+// The stencil of Eq. (3) at output site s (parity `parity`): accumulates into acc the products
+// of the site's 16 links (S = 1) -- or of its 8 fat (part 0) or 8 Naik links (part 1) when S = 2 --
+// with the neighbouring input vectors of the R right-hand sides r0.. that are active.
+template <int P, int NR, int R, int S, bool COHERENT>
+__device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat_f, const LinkField &naik_f, int parity,
+                                             const VecView<P> &vin, int s, int part, int r0, const bool act[R],
+                                             Cplx<typename Prec<P>::real> acc[R][3]) {
+    using real = typename Prec<P>::real;
+    using FatC = LinkCodec<P, 18>;
+    using NaikC = LinkCodec<P, NR>;
+    const SiteCoord sc = decode_site(g, s, parity);
+#pragma unroll
+    for (int kind = 0; kind < (S == 1 ? 2 : 1); kind++) {
+        const bool naik_kind = (S == 1) ? (kind == 1) : (part == 1);
+        const LinkField f = naik_kind ? naik_f : fat_f;
+        const int hop = naik_kind ? 3 : 1;
+        if (S == 1 && kind == 1 && NR != 18) {
+#pragma unroll
+            for (int grp = 0; grp < NaikC::GROUPS; grp++) {
+                uint32_t u[NaikC::WG * 4];
+                NaikC::load_group(naik_f, parity, g.Vh, s, grp, u);
+#pragma unroll
+                for (int l = 0; l < NaikC::G; l++) {
+                    const int slot = grp * NaikC::G + l;
+                    const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -3 : 3);
+                    Cplx<real> M[3][3];
+                    NaikC::decode(u, l, (real)1, M);
+                    Cplx<real> v[R][3];
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        if (act[r]) {
+                            load_vec<P, COHERENT>(vin, nb, r0 + r, v[r]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+                        }
+                    }
+                    matvec_acc<real, R>(M, v, acc);
+                }
+            }
+            continue;
+        }
+        real lscale = (real)1;
+        if (f.scale) lscale = (real)__ldg(f.scale + (size_t)parity * g.Vh + s);
+#pragma unroll
+        for (int grp = 0; grp < FatC::GROUPS; grp++) {
+            uint32_t u[FatC::WG * 4];
+            FatC::load_group(f, parity, g.Vh, s, grp, u);
+#pragma unroll
+            for (int l = 0; l < FatC::G; l++) {
+                const int slot = grp * FatC::G + l;
+                const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -hop : hop);
+                Cplx<real> M[3][3];
+                FatC::decode(u, l, lscale, M);
+                Cplx<real> v[R][3];
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    if (act[r]) {
+                        load_vec<P, COHERENT>(vin, nb, r0 + r, v[r]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+                    }
+                }
+                matvec_acc<real, R>(M, v, acc);
+            }
+        }
+    }
+}
+
+// S = 1: one thread applies all 16 links of its site.  S = 2 (18-real Naik only): two adjacent
+// lanes share a site, lane 0 applying the 8 fat links (hops of 1) and lane 1 the 8 Naik links
+// (hops of 3) with the same instruction stream, and one shuffle adds the halves: twice the
+// threads and half the dependent-load chain per thread when there are few right-hand sides.
 template <int P, int NR, int R, int EPI, int S>
 __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
     static_assert(S == 1 || (S == 2 && NR == 18), "the lane split needs identical fat and Naik encodings");
@@ -192,68 +266,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
 
-        if (valid) {
-            const SiteCoord sc = decode_site(g, s, a.parity);
-            // the kinds this lane applies: S = 1 both, S = 2 fat (part 0) or Naik (part 1)
-#pragma unroll
-            for (int kind = 0; kind < (S == 1 ? 2 : 1); kind++) {
-                const bool naik_kind = (S == 1) ? (kind == 1) : (part == 1);
-                const LinkField f = naik_kind ? a.naik : a.fat;
-                const int hop = naik_kind ? 3 : 1;
-                if (S == 1 && kind == 1 && NR != 18) {
-                    // 13- or 9-real Naik records (S = 1 only)
-#pragma unroll
-                    for (int grp = 0; grp < NaikC::GROUPS; grp++) {
-                        uint32_t u[NaikC::WG * 4];
-                        NaikC::load_group(a.naik, a.parity, g.Vh, s, grp, u);
-#pragma unroll
-                        for (int l = 0; l < NaikC::G; l++) {
-                            const int slot = grp * NaikC::G + l;
-                            const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -3 : 3);
-                            Cplx<real> M[3][3];
-                            NaikC::decode(u, l, (real)1, M);
-                            Cplx<real> v[R][3];
-#pragma unroll
-                            for (int r = 0; r < R; r++) {
-                                if (act[r]) {
-                                    load_vec<P>(vin, nb, r0 + r, v[r]);
-                                } else {
-#pragma unroll
-                                    for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
-                                }
-                            }
-                            matvec_acc<real, R>(M, v, acc);
-                        }
-                    }
-                    continue;
-                }
-                real lscale = (real)1;
-                if (f.scale) lscale = (real)__ldg(f.scale + (size_t)a.parity * g.Vh + s);
-#pragma unroll
-                for (int grp = 0; grp < FatC::GROUPS; grp++) {
-                    uint32_t u[FatC::WG * 4];
-                    FatC::load_group(f, a.parity, g.Vh, s, grp, u);
-#pragma unroll
-                    for (int l = 0; l < FatC::G; l++) {
-                        const int slot = grp * FatC::G + l;
-                        const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -hop : hop);
-                        Cplx<real> M[3][3];
-                        FatC::decode(u, l, lscale, M);
-                        Cplx<real> v[R][3];
-#pragma unroll
-                        for (int r = 0; r < R; r++) {
-                            if (act[r]) {
-                                load_vec<P>(vin, nb, r0 + r, v[r]);
-                            } else {
-#pragma unroll
-                                for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
-                            }
-                        }
-                        matvec_acc<real, R>(M, v, acc);
-                    }
-                }
-            }
-        }
+        if (valid) site_stencil<P, NR, R, S, false>(g, a.fat, a.naik, a.parity, vin, s, part, r0, act, acc);
         if constexpr (S == 2) {
             // add the fat and Naik halves; every lane of the warp takes part
 #pragma unroll

@@ -98,29 +98,40 @@ inline size_t vector_bytes(int prec, int Vh, int n) {
     }
 }
 
+// iterated precision of x and r for an inner (Dslash) precision: FP64 stays FP64, else FP32
+__host__ __device__ constexpr int q_prec(int p) { return p == HISQ_FP64 ? HISQ_FP64 : HISQ_FP32; }
+
 template <int P> struct VecView {
     void *data;
     int n;
 };
 
-template <int P>
+// COHERENT = true reads through L2 (ld.global.cg) instead of the read-only path: required for
+// data written earlier in the same kernel launch by other blocks (the persistent solver).
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T vld(const T *p) {
+    if constexpr (COHERENT) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <int P, bool COHERENT = false>
 __device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cplx<typename Prec<P>::real> w[3]) {
     if constexpr (P == HISQ_FP64) {
         const double2 *d = reinterpret_cast<const double2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            double2 x = __ldg(d + (long)c * v.n);
+            double2 x = vld<COHERENT>(d + (long)c * v.n);
             w[c] = {x.x, x.y};
         }
     } else if constexpr (P == HISQ_FP32) {
         const float2 *d = reinterpret_cast<const float2 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            float2 x = __ldg(d + (long)c * v.n);
+            float2 x = vld<COHERENT>(d + (long)c * v.n);
             w[c] = {x.x, x.y};
         }
     } else if constexpr (P == HISQ_FP16) {
-        uint4 q = __ldg(reinterpret_cast<const uint4 *>(v.data) + s * v.n + r);
+        uint4 q = vld<COHERENT>(reinterpret_cast<const uint4 *>(v.data) + s * v.n + r);
         const float sc = __uint_as_float(q.w);
         const uint32_t h[3] = {q.x, q.y, q.z};
 #pragma unroll
@@ -132,7 +143,7 @@ __device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cpl
         const __nv_bfloat162 *d = reinterpret_cast<const __nv_bfloat162 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            float2 f = __bfloat1622float2(__ldg(d + (long)c * v.n));
+            float2 f = __bfloat1622float2(vld<COHERENT>(d + (long)c * v.n));
             w[c] = {f.x, f.y};
         }
     }
@@ -307,6 +318,8 @@ void free_workspace(hisq_ctx *ctx);  // solver.cu
 void free_pc(hisq_pc *pc);           // pc.cu
 int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
                void *out, int n, cudaStream_t st);
+int pc_forward_hermitian(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                         const void *in, void *out, int n, cudaStream_t st);
 int pc_prepare(hisq_ctx *ctx, const hisq_pc *pc, int n);  // allocate the network workspace
 int pack_vectors(hisq_ctx *ctx, const double *canon_dev, void *internal, int n, int prec, cudaStream_t st);
 int unpack_vectors(hisq_ctx *ctx, const void *internal, double *canon_dev, int n, int prec, cudaStream_t st);

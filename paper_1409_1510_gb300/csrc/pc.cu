@@ -255,6 +255,55 @@ static int forward(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq
     return run_layer<4, 1, false>(ctx, naik, p, st);
 }
 
+// y = M^dag r on even sites: the adjoint layers in reverse order (L1^dag L2^dag L3^dag),
+// input r on even sites (zero on odd), output projected to even sites
+static int forward_adjoint(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const float2 *r,
+                           float2 *y, int K, cudaStream_t st) {
+    PcWork &w = pcw(pc);
+    for (int par = 0; par < 2; par++) {
+        PcLayerArgs p = layer_args(ctx, fat, naik, K, par);
+        p.W = layer_w(pc, 2);
+        p.in_same = par == 0 ? r : nullptr;
+        p.in_opp = par == 1 ? r : nullptr;
+        p.out = w.g2[par];
+        HISQ_CHECK((run_layer<1, 4, true>(ctx, naik, p, st)));
+    }
+    for (int par = 0; par < 2; par++) {
+        PcLayerArgs p = layer_args(ctx, fat, naik, K, par);
+        p.W = layer_w(pc, 1);
+        p.in_same = w.g2[par];
+        p.in_opp = w.g2[1 - par];
+        p.out = w.g1[par];
+        HISQ_CHECK((run_layer<4, 4, true>(ctx, naik, p, st)));
+    }
+    PcLayerArgs p = layer_args(ctx, fat, naik, K, 0);
+    p.W = layer_w(pc, 0);
+    p.in_same = w.g1[0];
+    p.in_opp = w.g1[1];
+    p.out = y;
+    return run_layer<4, 1, true>(ctx, naik, p, st);
+}
+
+// out = (a + b) / 2
+__global__ void pc_average_kernel(long n, const float2 *a, const float2 *b, float2 *out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float2 x = a[i], y = b[i];
+        out[i] = make_float2(0.5f * (x.x + y.x), 0.5f * (x.y + y.y));
+    }
+}
+
+// out = M_H in with M_H = (M + M^dag) / 2, the Hermitian part of the network
+static int forward_hermitian(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                             const float2 *in, float2 *out, int K, cudaStream_t st) {
+    PcWork &w = pcw(pc);
+    HISQ_CHECK(forward(ctx, pc, fat, naik, in, w.y, K, st));
+    HISQ_CHECK(forward_adjoint(ctx, pc, fat, naik, in, w.u, K, st));
+    const long n = (long)ctx->geom.Vh * 3 * K;
+    pc_average_kernel<<<(int)std::min<long>((n + 255) / 256, (long)ctx->num_sms * 8), 256, 0, st>>>(n, w.y, w.u, out);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
+}
+
 static RedArgs red_of(PcWork &w, double *dot_out) {
     RedArgs r;
     r.partials = w.partials;
@@ -425,6 +474,14 @@ int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hi
     return forward(ctx, m, fat, naik, reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out), n, st);
 }
 
+int pc_forward_hermitian(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                         const void *in, void *out, int n, cudaStream_t st) {
+    hisq_pc *m = const_cast<hisq_pc *>(pc);
+    HISQ_CHECK(ensure_work(ctx, m, n));
+    return forward_hermitian(ctx, m, fat, naik, reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out),
+                             n, st);
+}
+
 }  // namespace hisq
 
 using namespace hisq;
@@ -505,6 +562,16 @@ int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *na
     if (!in || !out || in == out) return set_error(HISQ_ERR_ARG, "bad vectors");
     if (nrhs < 1 || nrhs > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "nrhs must be in 1..%d", HISQ_MAX_BUNDLE);
     return pc_forward(ctx, pc, fat, naik, in, out, nrhs, ctx->stream);
+}
+
+int hisq_pc_apply_hermitian(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
+                            void *out, int nrhs) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    HISQ_CHECK(check_args(ctx, pc, fat, naik));
+    if (!in || !out || in == out) return set_error(HISQ_ERR_ARG, "bad vectors");
+    if (nrhs < 1 || nrhs > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "nrhs must be in 1..%d", HISQ_MAX_BUNDLE);
+    return pc_forward_hermitian(ctx, pc, fat, naik, in, out, nrhs, ctx->stream);
 }
 
 int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_links *naik, double mass, const void *r,

@@ -10,11 +10,10 @@
 
 #include "hisq_internal.cuh"
 #include "dslash_kernel.cuh"
+#include "cg_persistent.cuh"
 
 namespace hisq {
 
-// Sloppy (Dslash) precision P and the precision Q of the iterated x and r.
-__host__ __device__ constexpr int q_prec(int p) { return p == HISQ_FP64 ? HISQ_FP64 : HISQ_FP32; }
 
 struct BlasArgs {
     int Vh, n, spb;
@@ -351,6 +350,8 @@ struct Workspace {
     int d2_grid = 0;               // blocks of the last A-operator launch enqueued
     unsigned int *counter = nullptr;
     double *dots = nullptr;
+    unsigned int *bar = nullptr;   // persistent solve: grid-barrier arrivals and generation
+    int *err = nullptr;            // persistent solve: a barrier wait ran out
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     GraphCache gc;
 };
@@ -382,7 +383,9 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
             cudaMalloc(&w->partials, pcap * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&w->partials2, pcap * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&w->counter, sizeof(unsigned int) * 4) != cudaSuccess ||
-            cudaMalloc(&w->dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) != cudaSuccess)
+            cudaMalloc(&w->dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) != cudaSuccess ||
+            cudaMalloc(&w->bar, sizeof(unsigned int) * 4) != cudaSuccess ||
+            cudaMalloc(&w->err, sizeof(int) * 4) != cudaSuccess)
             return set_error(HISQ_ERR_NOMEM, "solver workspace allocation failed");
         w->partials_cap = pcap;
         cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
@@ -431,6 +434,8 @@ void free_workspace(hisq_ctx *ctx) {
     if (w->partials2) cudaFree(w->partials2);
     if (w->counter) cudaFree(w->counter);
     if (w->dots) cudaFree(w->dots);
+    if (w->bar) cudaFree(w->bar);
+    if (w->err) cudaFree(w->err);
     if (w->ev0) cudaEventDestroy(w->ev0);
     if (w->ev1) cudaEventDestroy(w->ev1);
     delete w;
@@ -451,6 +456,7 @@ struct Solve {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events;    // inner-precision Dslash
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events64;  // FP64 Dslash
     const hisq_pc *pc;                                           // flexible CG when set
+    bool persistent = false;                                     // solved by the persistent kernel
 };
 
 static BlasArgs blas_args(const Solve &S) {
@@ -603,7 +609,8 @@ static int enqueue_iteration_head(const Solve &S) {
 
 // flexible CG: z = M r (network); beta; p = z + beta p with <p, r>; then the CG head
 static int enqueue_fcg_head(const Solve &S) {
-    HISQ_CHECK(pc_forward(S.ctx, S.pc, S.fat, S.naik, S.w->r_lo, S.w->z, S.n, S.st));
+    // the Hermitian part of the network keeps the preconditioned recurrence a true PCG one
+    HISQ_CHECK(pc_forward_hermitian(S.ctx, S.pc, S.fat, S.naik, S.w->r_lo, S.w->z, S.n, S.st));
     HISQ_CHECK(blas(S, HOOK_FCG_BETA));
     HISQ_CHECK(blas(S, HOOK_FCG_PR));
     return enqueue_iteration_head(S);
@@ -731,11 +738,108 @@ static int build_graph(const Solve &S) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Persistent driver: the whole plain-CG solve of a bundle in one cooperative launch
+// ------------------------------------------------------------------------------------------
+static cudaError_t persistent_occ(int prec, int R, size_t smem, int *per_sm) {
+    switch (prec) {
+    case HISQ_FP64: return persistent_occupancy<HISQ_FP64>(R, smem, per_sm);
+    case HISQ_FP32: return persistent_occupancy<HISQ_FP32>(R, smem, per_sm);
+    case HISQ_FP16: return persistent_occupancy<HISQ_FP16>(R, smem, per_sm);
+    default: return persistent_occupancy<HISQ_BF16>(R, smem, per_sm);
+    }
+}
+
+static cudaError_t persistent_launch(int prec, const PersArgs &a, int R, int grid, size_t smem, cudaStream_t st) {
+    switch (prec) {
+    case HISQ_FP64: return launch_persistent_prec<HISQ_FP64>(a, R, grid, smem, st);
+    case HISQ_FP32: return launch_persistent_prec<HISQ_FP32>(a, R, grid, smem, st);
+    case HISQ_FP16: return launch_persistent_prec<HISQ_FP16>(a, R, grid, smem, st);
+    default: return launch_persistent_prec<HISQ_BF16>(a, R, grid, smem, st);
+    }
+}
+
+// Runs the bundle in the persistent kernel when it applies (plain CG, 18-real Naik links and a
+// co-resident grid); *done = false leaves the bundle to the graph driver.
+static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
+    *done = false;
+    if (S.pc || S.naik->recon != 18) return HISQ_OK;
+    Workspace *w = S.w;
+    LaunchShape sh = tuned_shape(S.ctx, S.fat, S.naik, S.n, S.prec == HISQ_FP64);
+    int R = sh.R > 4 ? 4 : sh.R;
+    if (S.prec == HISQ_FP64 && R > 2) R = 2;  // four FP64 right-hand sides per thread would spill
+    while (S.n % R) R /= 2;
+    const size_t smem = (size_t)(256 * R + 64) * sizeof(double);
+    int per_sm = 0;
+    if (persistent_occ(S.prec, R, smem, &per_sm) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return HISQ_OK;
+    }
+    const int grid = per_sm * S.ctx->num_sms;  // one wave: every block resident (cooperative launch)
+    if ((size_t)grid * PERS_ND > w->partials_cap) return HISQ_OK;
+    PersArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = S.ctx->geom;
+    a.fat = S.fat->field();
+    a.naik = S.naik->field();
+    a.fat64 = S.fat->field64();
+    a.naik64 = S.naik->field64();
+    if (S.prec == HISQ_FP64) {
+        a.fat = a.fat64;
+        a.naik = a.naik64;
+    }
+    a.p = w->p;
+    a.t = w->t;
+    a.ap = w->Ap;
+    a.x = w->x_lo;
+    a.r = w->r_lo;
+    a.b = w->b_hi;
+    a.xhi = w->x_hi;
+    a.t64 = w->t64;
+    a.mass2 = S.mass * S.mass;
+    a.n = S.n;
+    a.partials = w->partials;
+    a.st = w->st;
+    a.bar = w->bar;
+    a.err = w->err;
+    a.spin_limit = 1LL << 22;  // a barrier wait gives up after about a second
+    a.expected = grid;
+    if (S.ctx->params.debug_barrier_timeout) {  // test hook: no barrier can complete
+        a.expected = grid + 1;
+        a.spin_limit = 1LL << 12;
+    }
+    HISQ_CHECK(set_state_params(S, 0, 0, tol));
+    HISQ_CHECK(pack_vectors(S.ctx, w->canon, w->b_hi, S.n, HISQ_FP64, S.st));
+    HISQ_CUDA(cudaMemsetAsync(w->bar, 0, sizeof(unsigned int) * 4, S.st));
+    HISQ_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int) * 4, S.st));
+    cudaError_t e = persistent_launch(S.prec, a, R, grid, smem, S.st);
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return HISQ_OK;  // not co-resident here: the graph driver takes the bundle
+    }
+    if (e != cudaSuccess) return set_error(HISQ_ERR_CUDA, "persistent solve launch failed: %s", cudaGetErrorString(e));
+    int err_h = 0;
+    HISQ_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(SolverState), cudaMemcpyDeviceToHost, S.st));
+    HISQ_CUDA(cudaMemcpyAsync(&err_h, w->err, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    HISQ_CUDA(cudaStreamSynchronize(S.st));
+    if (err_h) return set_error(HISQ_ERR_TIMEOUT, "a grid barrier of the persistent solve ran out of its wait budget");
+    *done = true;
+    return HISQ_OK;
+}
+
+// ------------------------------------------------------------------------------------------
 // One bundle
 // ------------------------------------------------------------------------------------------
 static int solve_bundle(Solve &S, double tol) {
     Workspace *w = S.w;
     const hisq_solver_params &P = S.ctx->params;
+    if (P.use_graph == 2 && !S.timing) {
+        bool done = false;
+        HISQ_CHECK(solve_bundle_persistent(S, tol, &done));
+        if (done) {
+            S.persistent = true;
+            return HISQ_OK;
+        }
+    }
     bool graph = P.use_graph && !S.timing;
     if (graph) {
         bool reuse = w->gc.exec && w->gc.fat == S.fat && w->gc.naik == S.naik && w->gc.mass == S.mass &&
@@ -875,8 +979,12 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
         // p-update; the three residual-recomputation kernels run when an update is due (graph)
         // or are launched every iteration as gated no-ops (host-driven)
         bool graph_mode = P.use_graph && !S.timing;
-        long per_iter = P.pc ? 3 + 5 + 2 : 4;  // flexible CG: 5 network layers, beta and direction kernels
-        stats.kernel_launches += 3 + per_iter * h.bundle_iters + 3L * (graph_mode ? h.update_rounds : h.bundle_iters);
+        long per_iter = P.pc ? 3 + 11 + 2 : 4;  // flexible CG: M and M^dag (5 layers each) and their average,
+                                                 // beta and direction kernels
+        if (S.persistent)
+            stats.kernel_launches += 3;  // pack b, the persistent solve, unpack x
+        else
+            stats.kernel_launches += 3 + per_iter * h.bundle_iters + 3L * (graph_mode ? h.update_rounds : h.bundle_iters);
         stats.bundle_iterations += bmax;
         stats.bundles++;
     }

@@ -31,7 +31,8 @@ class hisq_solver_params(ctypes.Structure):
     _fields_ = [("inner_prec", ctypes.c_int), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("bundle", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("pc", ctypes.c_void_p), ("stall_window", ctypes.c_int), ("stall_factor", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int),
+                ("debug_barrier_timeout", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGNATURES = {
     "hisq_pc_set_weights": ([_VP, _VP], _I),
     "hisq_pc_get_weights": ([_VP, _VP], _I),
     "hisq_pc_apply": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
+    "hisq_pc_apply_hermitian": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_loss_grad": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _VP, _VP], _I),
     "hisq_pc_adam_step": ([_VP, _VP, _I, _D, _D, _D, _D], _I),
     "hisq_pc_train": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _I, _I, _D, _VP], _I),
@@ -248,6 +250,10 @@ def hisq_pc_get_weights(pc, weights):
 
 def hisq_pc_apply(pc, fat, naik, vin, vout, nrhs: int):
     _check(load().hisq_pc_apply(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
+
+
+def hisq_pc_apply_hermitian(pc, fat, naik, vin, vout, nrhs: int):
+    _check(load().hisq_pc_apply_hermitian(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
 
 
 def hisq_pc_loss_grad(pc, fat, naik, mass: float, r, e, K: int, grad):

@@ -223,3 +223,25 @@ def test_fcg_stall_falls_back_to_cg():
         x, stats, iters = _fcg(g, pc, rhs, mass, 1, stall_window=5)
         assert g.oracle.true_residual(rhs[0], x[0], mass)[0] <= TOL * 1.01
         assert stats.fallbacks >= 1
+
+
+def test_hermitian_part_of_the_network():
+    """M_H = (M + M^dag)/2 applied by the GPU: <u, M_H v> = (<u, M v> + <M u, v>)/2 with M the
+    oracle's network, and M_H is Hermitian: <u, M_H v> = conj(<v, M_H u>)."""
+    with gpu(DIMS, 1) as g:
+        W = _weights(5, 0.3)
+        pc = g.hisq.hisq_pc_create(_as_real(W))
+        u = hi.gaussian_rhs(g.lat, 800)
+        v = hi.gaussian_rhs(g.lat, 801)
+        mh = _apply_h(g, pc, np.stack([u, v]))
+        lhs = np.vdot(u, mh[1])
+        want = 0.5 * (np.vdot(u, g.oracle.pc_forward(W, v)) + np.vdot(g.oracle.pc_forward(W, u), v))
+        assert abs(lhs - want) / abs(want) <= 3e-5
+        assert abs(lhs - np.conj(np.vdot(v, mh[0]))) / abs(lhs) <= 3e-5
+
+
+def _apply_h(g, pc, v):
+    n = len(v)
+    vin, vout = g.pack(v, 1), g.bundle(n, 1)
+    g.hisq.hisq_pc_apply_hermitian(pc, g.fat, g.naik, vin, vout, n)
+    return g.unpack(vout, n, 1)

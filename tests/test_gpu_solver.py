@@ -31,7 +31,7 @@ def test_config0_plain_fp64():
     dims = (8, 8, 8, 4)
     with gpu(dims, 0) as g:
         b = hi.gaussian_rhs(g.lat, 0)
-        for graph in (0, 1):
+        for graph in (0, 1, 2):
             x, stats, iters, res = _solve(g, [b], 0.1, inner_prec=0, use_graph=graph)
             true = g.oracle.true_residual(b, x[0], 0.1)[0]
             assert true <= TOL * SLACK and res[0] <= TOL
@@ -40,7 +40,7 @@ def test_config0_plain_fp64():
 
 
 @pytest.mark.parametrize("prec", [1, 2, 3])
-@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("graph", [0, 1, 2])
 def test_mixed_precision_reaches_fp64_residual(prec, graph):
     dims = (8, 10, 8, 6)
     with gpu(dims, prec) as g:
@@ -51,7 +51,7 @@ def test_mixed_precision_reaches_fp64_residual(prec, graph):
         assert stats.converged == 3 and stats.reliable_updates >= 3
 
 
-@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("graph", [0, 1, 2])
 def test_bundle_uneven_convergence_masked(graph):
     """A bundle whose right-hand sides converge at different iterations (scaled norms 1e-3..1e3
     and spectral shaping b = A^q g): converged ones are masked while the rest iterate."""
@@ -136,3 +136,36 @@ def test_plain_fp64_cg_on_lower_precision_links():
         assert g.oracle.true_residual(b, x[0], 0.05)[0] <= TOL * SLACK
         _, it_oracle, _ = g.oracle.cg(b, 0.05, TOL)
         assert abs(int(iters[0]) - it_oracle) <= 2
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_persistent_matches_graph_iterations(prec):
+    """The persistent kernel runs the same algorithm as the graph driver: same iteration counts
+    and reliable updates, and the FP64 true residual met."""
+    dims = (8, 10, 8, 6)
+    with gpu(dims, prec) as g:
+        rhs = [hi.gaussian_rhs(g.lat, 60 + k) for k in range(4)]
+        _, s1, it1, _ = _solve(g, rhs, 0.05, inner_prec=prec, use_graph=1, bundle=4)
+        x2, s2, it2, _ = _solve(g, rhs, 0.05, inner_prec=prec, use_graph=2, bundle=4)
+        assert np.array_equal(it1, it2) and s1.reliable_updates == s2.reliable_updates
+        assert s2.kernel_launches == 3
+        true = g.oracle.true_residual(np.stack(rhs), x2, 0.05)
+        assert np.all(true <= TOL * SLACK)
+
+
+def test_persistent_barrier_timeout_is_reported_and_context_survives():
+    """Failure detection without a fault: the test hook makes every grid barrier wait for a block
+    that does not exist; the bounded waits run out, the kernel returns, the solve reports
+    HISQ_ERR_TIMEOUT, and the same context then solves normally."""
+    dims = (8, 8, 8, 4)
+    with gpu(dims, 1) as g:
+        b = hi.gaussian_rhs(g.lat, 0)
+        p = g.hisq.hisq_default_solver_params()
+        p.use_graph = 2
+        p.debug_barrier_timeout = 1
+        g.hisq.hisq_set_solver_params(p)
+        x = np.zeros_like(b)
+        rc = g.hisq.hisq_cg_solve(g.fat, g.naik, [b], [x], 0.1, TOL, raise_on_error=False)
+        assert rc == -6
+        x, stats, iters, res = _solve(g, [b], 0.1, inner_prec=1, use_graph=2)
+        assert g.oracle.true_residual(b, x[0], 0.1)[0] <= TOL * SLACK
