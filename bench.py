@@ -133,9 +133,9 @@ def peaks():
 
 
 def kernel_traffic(dims, inner):
-    """dram bytes per launch of the inner Dslash from the committed ncu summary, if that summary
-    was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    """DRAM bytes (read + write) per launch of the persistent solve kernel from the committed
+    ncu summary, if that summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -143,15 +143,19 @@ def kernel_traffic(dims, inner):
         return None
     if rec.get("source_sha") != kernel_source_hash():
         return None
-    key = f"{inner}_{'x'.join(map(str, dims))}"
+    key = f"cg_persistent_{inner}_{'x'.join(map(str, dims))}"
     val = rec.get("per_launch_bytes", {}).get(key)
     return float(val) if val else None
+
+
+KERNEL_SOURCES = ("cg_persistent.cuh", "cg_persistent_body.cuh", "dslash_kernel.cuh", "link_codec.cuh",
+                  "hisq_internal.cuh", "solver_state.cuh")
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1409_1510_gb300", "csrc")
-    for name in ("dslash_kernel.cuh", "link_codec.cuh", "hisq_internal.cuh"):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -281,12 +285,13 @@ def run_ours(args, rank, world, local_rank, dist):
     timed(1, inner, 0, 1)
     timed(1, 0, 2)
 
-    # ---- the timed region: K mixed-precision solves (persistent driver) ----
+    # ---- the timed region: K mixed-precision solves (persistent driver, the kernel and its
+    # phases timed on the solve's stream) ----
     with ClockSampler(local_rank) as clk:
         barrier()
         clk.mark(True)
         t_wall = time.perf_counter()
-        ms, stats = timed(args.steps, inner, 2)
+        ms, stats = timed(args.steps, inner, 2, 1)
         barrier()
         t_wall = time.perf_counter() - t_wall
         clk.mark(False)
@@ -310,7 +315,37 @@ def run_ours(args, rank, world, local_rank, dist):
     gms, _ = timed(max(3, min(args.steps, 10)), inner, 1)
     graph_ms = statistics.median(gms)
 
-    # ---- roofline of the inner Dslash: host-driven solves with CUDA events on every launch ----
+    # ---- roofline of the dominant kernel, the persistent solve kernel of the timed region:
+    # algorithmic bytes of each launch (setup, iterations, FP64 recomputations) over its
+    # CUDA-event duration; phase times from inside the kernel ----
+    hbm_peak, peak_kind = peaks()
+    Vh = lat.half_volume
+    k_ms = sum(s.solve_kernel_ms for s in stats)
+    k_n = sum(s.solve_kernel_launches for s in stats)
+    k_bytes = sum(acc.cg_solve_bytes(inner, Vh, s.bundle_iterations, s.reliable_updates) for s in stats)
+    k_achieved = k_bytes / (k_ms / 1e3) / 1e9
+    ph = [sum(s.phase_ms[i] for s in stats) for i in range(5)]
+    its = sum(s.bundle_iterations for s in stats)
+    ups = sum(s.reliable_updates for s in stats)
+    P_b = acc.VECTOR_BYTES[inner]
+    ds_bytes = its * (2 * acc.LINK_BYTES_18[inner] + 5 * P_b) * Vh          # D_oe p and A p phases
+    ds_gbs = ds_bytes / ((ph[0] + ph[1]) / 1e3) / 1e9 if ph[0] + ph[1] > 0 else None
+    rel_gflops = ups * 2 * acc.DSLASH_FLOPS_PER_SITE * Vh / (ph[3] / 1e3) / 1e9 if ph[3] > 0 else None
+    phases = {"ms_per_launch": {name: ph[i] / max(k_n, 1) for i, name in
+                                enumerate(("dslash_doe", "dslash_aop_dot", "xr_update", "fp64_reliable", "p_update"))},
+              "dslash_phases_gbs": ds_gbs, "dslash_phases_frac": ds_gbs / hbm_peak if ds_gbs else None,
+              "fp64_reliable_gflops": rel_gflops,
+              "fp64_reliable_share": ph[3] / k_ms if k_ms > 0 else None,
+              "clock": "%globaltimer read by block 0 after each grid barrier"}
+    traffic = kernel_traffic(dims, args.inner)
+    roofline = {"bound": "hbm", "achieved": k_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": k_achieved / hbm_peak, "traffic": traffic,
+                "kernel": f"cg_persistent_kernel<{args.inner}> (whole solve, {k_n} launches timed in the timed region)",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": k_bytes / max(k_n, 1),
+                "launch_ms": k_ms / max(k_n, 1), "phases": phases}
+
+    # ---- the inner Dslash as separate kernels: host-driven solves, CUDA events on every launch ----
     kr = max(3, min(args.steps, 10))
     _, rstats = timed(kr, inner, 0, 1)
     d_ms = sum(s.dslash_ms for s in rstats)
@@ -326,14 +361,7 @@ def run_ours(args, rank, world, local_rank, dist):
     vec_b = acc.VECTOR_REALS * elem + vec_scale
     bytes_per_launch = (link_b + 2.5 * vec_b) * lat.half_volume
     avg_s = d_ms / max(d_n, 1) / 1e3
-    hbm_peak, peak_kind = peaks()
     achieved = bytes_per_launch / avg_s / 1e9
-    traffic = kernel_traffic(dims, args.inner)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
-                "kernel": f"dslash_kernel<{args.inner}, naik 18> inside the solve ({d_n} launches timed)",
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "algorithmic_bytes_per_launch": bytes_per_launch}
     dslash_gflops = acc.DSLASH_FLOPS_PER_SITE * lat.half_volume / avg_s / 1e9
     # the FP64 residual Dslash on its own (FP64 arithmetic bound): n = 1, CUDA events, L2 flushed
     fat64 = hisq.hisq_links_create(d64(X), False, 0, 18)
@@ -412,8 +440,11 @@ def run_ours(args, rank, world, local_rank, dist):
             "cg_s_per_rhs": s_rhs, "fp64_cg_s_per_rhs": fp64_s, "speedup_vs_fp64_cg": fp64_s / s_rhs,
             "iterations": iters, "reliable_updates": stats[-1].reliable_updates, "true_residual": float(res[0]),
             "fp64_cg_iterations": st64[-1].max_iterations,
-            "dslash": {"gflops": dslash_gflops, "hbm_gbs": achieved, "precision": args.inner,
-                       "fp64_residual_dslash_gflops": fp64_dslash_gflops, "nrhs": 1},
+            "dslash": {"gflops": dslash_gflops, "hbm_gbs": achieved, "frac_hbm": achieved / hbm_peak,
+                       "precision": args.inner, "nrhs": 1,
+                       "kernel": f"dslash_kernel<{args.inner}, naik 18>, host-driven solves ({d_n} launches, CUDA events)",
+                       "algorithmic_bytes_per_launch": bytes_per_launch,
+                       "fp64_residual_dslash_gflops": fp64_dslash_gflops},
             "host_driven_ms_per_step": host_ms, "graph_driver_ms_per_step": graph_ms,
             "other_inner_precisions": variants,
             "bundle_of_16": dict(batched, speedup_per_rhs_vs_single=s_rhs / batched["s_per_rhs"]),

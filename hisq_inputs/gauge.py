@@ -13,7 +13,8 @@ Conventions (shared by every consumer of these arrays):
 The fields follow the synthetic recipe used throughout this project:
 
 * random SU(3): ``U = exp(i * eps * H)`` with ``H = sum_a h_a lambda_a / 2``, ``h_a ~ N(0,1)``
-  (Gell-Mann basis), computed through the Hermitian eigendecomposition of H;
+  (Gell-Mann basis), computed with the Cayley-Hamilton closed form of exp(iQ) for traceless
+  Hermitian Q (Morningstar and Peardon 2004), equal to the spectral definition to rounding;
 * fat link: ``X_{x,mu} = eta_mu(x) b_mu(x) (U_{x,mu} o (1 + 0.05 xi))`` with xi an i.i.d.
   complex Gaussian per matrix entry (E|xi|^2 = 1), so X is not unitary, like a smeared link;
 * Naik link: ``N_{x,mu} = eta_mu(x) b3_mu(x) (-1/24) U'_{x,mu} U'_{x+mu,mu} U'_{x+2mu,mu}``
@@ -85,12 +86,54 @@ class Lattice:
         return a.reshape(a.shape[:1] + (lt, lz, ly, lx) + a.shape[2:])
 
 
+def _exp_i_traceless_hermitian(q: np.ndarray) -> np.ndarray:
+    """exp(iQ) for a batch of traceless Hermitian 3x3 matrices by the Cayley-Hamilton closed form
+    of Morningstar and Peardon (2004): exp(iQ) = f0 + f1 Q + f2 Q^2, with the f_j functions of
+    c0 = det Q and c1 = tr(Q^2) / 2 only.  Vectorised over the batch; matches the spectral
+    definition q exp(i w) q^dagger to rounding."""
+    q2 = np.einsum("nij,njk->nik", q, q)
+    c1 = 0.5 * np.einsum("nii->n", q2).real
+    c0 = (q[:, 0, 0] * (q[:, 1, 1] * q[:, 2, 2] - q[:, 1, 2] * q[:, 2, 1])
+          - q[:, 0, 1] * (q[:, 1, 0] * q[:, 2, 2] - q[:, 1, 2] * q[:, 2, 0])
+          + q[:, 0, 2] * (q[:, 1, 0] * q[:, 2, 1] - q[:, 1, 1] * q[:, 2, 0])).real
+    neg = c0 < 0
+    c0 = np.abs(c0)                       # f_j(-c0) = (-1)^j conj(f_j(c0))
+    tiny = c1 < 1e-14
+    c1s = np.where(tiny, 1.0, c1)
+    c0max = 2.0 * (c1s / 3.0) ** 1.5
+    theta = np.arccos(np.clip(c0 / c0max, -1.0, 1.0))
+    u = np.sqrt(c1s / 3.0) * np.cos(theta / 3.0)
+    w = np.sqrt(c1s) * np.sin(theta / 3.0)
+    w2 = w * w
+    small = np.abs(w) < 0.05
+    xi0 = np.where(small, 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)),
+                   np.sin(w) / np.where(small, 1.0, w))
+    e2iu, emiu = np.exp(2j * u), np.exp(-1j * u)
+    cw = np.cos(w)
+    u2 = u * u
+    h0 = (u2 - w2) * e2iu + emiu * (8.0 * u2 * cw + 2j * u * (3.0 * u2 + w2) * xi0)
+    h1 = 2.0 * u * e2iu - emiu * (2.0 * u * cw - 1j * (3.0 * u2 - w2) * xi0)
+    h2 = e2iu - emiu * (cw + 3j * u * xi0)
+    den = 9.0 * u2 - w2
+    f = [h / den for h in (h0, h1, h2)]
+    f = [np.where(neg, (-1) ** j * np.conj(fj), fj) for j, fj in enumerate(f)]
+    eye = np.eye(3)
+    out = f[0][:, None, None] * eye + f[1][:, None, None] * q + f[2][:, None, None] * q2
+    if np.any(tiny):                      # Q ~ 0: the series to second order is exact to rounding
+        qt, q2t = q[tiny], q2[tiny]
+        out[tiny] = eye + 1j * qt - 0.5 * q2t
+    return out
+
+
 def random_su3(rng: np.random.Generator, count: int, eps: float) -> np.ndarray:
     """``count`` matrices exp(i*eps*H), H = sum_a h_a lambda_a/2 with h_a ~ N(0, 1)."""
     h = rng.standard_normal((count, 8))
-    herm = np.einsum("na,aij->nij", h, _GELL_MANN / 2)
-    w, q = np.linalg.eigh(herm)
-    return (q * np.exp(1j * eps * w)[:, None, :]) @ q.conj().swapaxes(-1, -2)
+    out = np.empty((count, 3, 3), np.complex128)
+    chunk = 1 << 20
+    for i0 in range(0, count, chunk):
+        q = eps * np.einsum("na,aij->nij", h[i0:i0 + chunk], _GELL_MANN / 2)
+        out[i0:i0 + chunk] = _exp_i_traceless_hermitian(q)
+    return out
 
 
 def staggered_phases(lat: Lattice) -> np.ndarray:

@@ -83,7 +83,7 @@ int hisq_finalize(void);
 const char *hisq_strerror(int status);
 const char *hisq_last_error(void);
 
-/* ---- links (row a1 of the hot path: pack once per gauge field) ------------------------------ */
+/* ---- links (packed once per gauge field) -------------------------------------------------- */
 
 /* Pack one kind of link field for the Dslash.  canon: host or device, canonical layout
  * double[4][V][3][3][2], the fat links X (is_naik = 0, hop 1) or the Naik links N (is_naik = 1,
@@ -110,7 +110,7 @@ size_t hisq_vector_bytes(int prec, int nrhs);
 int hisq_pack(const double *canon, void *internal, int nrhs, int prec);
 int hisq_unpack(const void *internal, double *canon, int nrhs, int prec);
 
-/* ---- operators (rows a2, a3) -------------------------------------------------------------- */
+/* ---- operators ---------------------------------------------------------------------------- */
 
 /* w = D_{p,1-p} v for nrhs (1..HISQ_MAX_NRHS) right-hand sides, Eq. (3)-(4): the input lives on
  * parity 1-parity and the output on `parity` (0: D_eo, odd -> even; 1: D_oe, even -> odd).
@@ -126,7 +126,7 @@ int hisq_dslash(const hisq_links *fat, const hisq_links *naik, const void *in, v
 int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
              void *out, int nrhs, double *pAp);
 
-/* ---- A-operator without allocation ---------------------------------------------------------- */
+/* ---- A-operator without allocation -------------------------------------------------------- */
 
 /* Size of the static device scratch behind hisq_aop_noalloc (per device, held until exit). */
 #define HISQ_AOP_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -152,7 +152,7 @@ int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const v
 int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
                      void *out, int nrhs, double *pAp);
 
-/* ---- solvers (rows a4-a6, a9) ------------------------------------------------------------- */
+/* ---- solvers ------------------------------------------------------------------------------ */
 
 typedef struct {
     int inner_prec;       /* HISQ_FP64: plain FP64 CG; FP32/FP16/BF16: mixed precision with FP64
@@ -170,7 +170,8 @@ typedef struct {
     int stall_window;     /* flexible CG: fall back to plain CG if the residual does not drop */
     double stall_factor;  /* by stall_factor within stall_window iterations (10, 50) */
     int autotune;         /* 1: time the Dslash launch shapes on first use of a shape */
-    int time_kernels;     /* 1: record CUDA events around every Dslash launch (stats) */
+    int time_kernels;     /* 1: record CUDA events around every Dslash launch (host-driven) or
+                             around each persistent solve kernel, with its phase times (stats) */
     int debug_barrier_timeout; /* test hook for failure detection: 1 makes every grid barrier of
                              the persistent solve wait for one block more than it launches, so the
                              bounded waits run out and the solve returns HISQ_ERR_TIMEOUT */
@@ -207,6 +208,13 @@ typedef struct {
     int dslash64_launches;
     double flops;             /* useful flops: (2*1146 + 72) per even site, RHS and iteration */
     long kernel_launches;     /* kernels of this library launched by the solve */
+    double solve_kernel_ms;   /* summed duration of the persistent solve kernels (use_graph = 2,
+                                 time_kernels = 1; CUDA events on the solve's stream) */
+    int solve_kernel_launches;
+    double phase_ms[5];       /* inside those kernels, block 0's time from one grid barrier to the
+                                 next, summed per phase: [0] D_oe p, [1] A p = m^2 p - D_eo t with
+                                 <p, A p>, [2] x, r update with |r|^2, [3] FP64 residual
+                                 recomputations, [4] p = r + beta p (each with its scalar step) */
 } hisq_solve_stats;
 
 /* Statistics of the calling thread's last hisq_cg_solve.  iterations (int[nrhs]) and
@@ -215,21 +223,23 @@ typedef struct {
 int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual);
 
 /* Pick and cache the fastest Dslash launch shape for nrhs right-hand sides in the links'
- * precision (row a6), timing every candidate with CUDA events after an L2 flush.  Writes the
- * chosen right-hand sides per thread, threads per block and lanes per site (1, or 2 when the fat
- * and Naik halves of a site run on two lanes) if the pointers are not NULL.  Allocates its
+ * precision, timing every candidate with CUDA events after an L2 flush.  Writes the
+ * chosen right-hand sides per thread, threads per block and lanes per site (1; 2 when the fat
+ * and Naik halves of a site run on two lanes; 4 when each lane takes two directions of one kind)
+ * if the pointers are not NULL.  Allocates its
  * timing buffers. */
 int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int nrhs, int *rhs_per_thread,
                   int *block_threads, int *lanes_per_site);
 
 /* Pin the Dslash launch shape used for nrhs right-hand sides with links of (prec, recon):
  * rhs_per_thread in {1, 2, 4, 8} dividing nrhs (FP64: 1, 2, 4), block_threads in 32..256,
- * lanes_per_site 1 or 2 (2 only with 18-real Naik links and rhs_per_thread <= 4).
+ * lanes_per_site 1, 2 (18-real Naik links, rhs_per_thread <= 4) or 4 (18-real Naik links,
+ * rhs_per_thread <= 2).
  * Overrides the autotuner's choice for that key. */
 int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_thread, int block_threads,
                           int lanes_per_site);
 
-/* ---- learned preconditioner (rows a7-a9) --------------------------------------------------- */
+/* ---- learned preconditioner --------------------------------------------------------------- */
 
 /* A gauge-covariant parallel-transport network, channels 1 -> 4 -> 4 -> 1, 17 paths per layer
  * (identity, T^{+-1}_mu through X, T^{+-3}_mu through N), complex weights stored as

@@ -45,3 +45,44 @@ def compulsory_bytes(nrhs: int, link_real_bytes: float, vector_real_bytes: float
     input vector once and each output vector once (plus per-(site, RHS) scales if any)."""
     vec = VECTOR_REALS * vector_real_bytes + vector_scale_bytes
     return link_bytes_per_site(link_real_bytes, naik_reals, fat_scale_bytes) + 2 * vec * nrhs
+
+
+# ---- the whole mixed-precision CG solve (algorithmic bytes per even site and RHS) ----------------
+# Storage per colour vector of one site and right-hand side: FP64 48 B, FP32 24 B, FP16 12 B plus
+# a 4 B scale, BF16 12 B.  The iterated x and r are FP32 unless the inner precision is FP64.
+VECTOR_BYTES = {0: 48.0, 1: 24.0, 2: 16.0, 3: 12.0}
+LINK_BYTES_18 = {0: 2 * 8 * 18 * 8.0, 1: 2 * 8 * 18 * 4.0, 2: 2 * 8 * 18 * 2.0 + 8.0, 3: 2 * 8 * 18 * 2.0 + 8.0}
+
+
+def cg_iteration_bytes(prec: int, nrhs: int = 1) -> float:
+    """One iteration of a bundle, per even site, with 18-real links read once for the bundle:
+    t = D_oe p (links; p, t), A p = m^2 p - D_eo t (links; t, p, Ap), x += alpha p and
+    r -= alpha A p (p, Ap read; x, r read and written), p = r + beta p (r read; p read and
+    written): 2 links + nrhs (9 P + 5 Q) bytes."""
+    P = VECTOR_BYTES[prec]
+    Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
+    return 2 * LINK_BYTES_18[prec] + nrhs * (9 * P + 5 * Q)
+
+
+def reliable_update_bytes(prec: int, nrhs: int = 1) -> float:
+    """One FP64 residual recomputation of a bundle, per even site: x_hi += x (x read and zeroed,
+    x_hi read and written), t = D_oe x_hi (FP64 links; x_hi, t), r = b - m^2 x_hi + D_eo t (FP64
+    links; t, x_hi, b read; r written in the iterated precision)."""
+    Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
+    L64 = LINK_BYTES_18[0]
+    return 2 * L64 + nrhs * ((2 * Q + 96.0) + 96.0 + (144.0 + Q))
+
+
+def cg_setup_bytes(prec: int, nrhs: int = 1) -> float:
+    """Setup of a bundle per even site: b read; x_hi, x, r, p written."""
+    P = VECTOR_BYTES[prec]
+    Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
+    return nrhs * (96.0 + 2 * Q + P)
+
+
+def cg_solve_bytes(prec: int, half_volume: int, iterations: int, reliable_updates: int, nrhs: int = 1) -> float:
+    """Algorithmic bytes of one bundle solve whose nrhs right-hand sides all ran `iterations`
+    iterations and `reliable_updates` FP64 recomputations."""
+    per = (cg_setup_bytes(prec, nrhs) + iterations * cg_iteration_bytes(prec, nrhs)
+           + reliable_updates * reliable_update_bytes(prec, nrhs))
+    return per * half_volume

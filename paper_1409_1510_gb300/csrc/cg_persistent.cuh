@@ -28,7 +28,48 @@ struct PersArgs {
     int *err;
     long long spin_limit;
     unsigned int expected;    // arrivals that complete a barrier (gridDim.x; more only to test timeouts)
+    unsigned long long *phase_ns;  // [PERS_PHASES] time per phase as seen by block 0, or null
 };
+
+// Phases of the persistent solve, timed by block 0 from one grid barrier to the next: the
+// first Dslash (D_oe p), the second with its epilogue (A p, <p, A p>), the x / r update with
+// |r|^2, the FP64 residual recomputations, and the direction update (each phase includes the
+// scalar step and barrier that end it).
+enum PersPhase { PH_DOE = 0, PH_AOP = 1, PH_UPDATE = 2, PH_RELIABLE = 3, PH_PUPDATE = 4, PERS_PHASES = 5 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Block 0, thread 0 charges the time since the previous mark to `phase` (no-op otherwise).  The
+// clock lives in shared memory so that it costs the other threads no registers.
+struct PhaseClock {
+    unsigned long long last, acc[PERS_PHASES];
+    int on;
+};
+
+__device__ __forceinline__ void clock_start(PhaseClock &c, const unsigned long long *out) {
+    if (threadIdx.x == 0) {
+        c.on = out != nullptr && blockIdx.x == 0;
+        for (int i = 0; i < PERS_PHASES; i++) c.acc[i] = 0;
+        c.last = c.on ? global_ns() : 0;
+    }
+}
+
+__device__ __forceinline__ void clock_mark(PhaseClock &c, int phase) {
+    if (threadIdx.x == 0 && c.on) {
+        const unsigned long long now = global_ns();
+        c.acc[phase] += now - c.last;
+        c.last = now;
+    }
+}
+
+__device__ __forceinline__ void clock_store(const PhaseClock &c, unsigned long long *out) {
+    if (threadIdx.x == 0 && c.on)
+        for (int i = 0; i < PERS_PHASES; i++) out[i] = c.acc[i];
+}
 
 constexpr int PERS_ND = 2 * HISQ_MAX_BUNDLE;
 

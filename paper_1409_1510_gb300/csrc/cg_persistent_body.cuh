@@ -65,17 +65,21 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         if (tid == 0) run_hook(HOOK_INIT, &st, dots, n);
         __syncthreads();
     }
+    __shared__ PhaseClock clk;
+    clock_start(clk, a.phase_ns);
 
     while (ok && st.any_active && st.bundle_iters < st.max_iter) {
         // t = D_oe p
         dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, a.p, a.t, 1, st.active, nullptr, nullptr, nullptr, red);
         if (!(ok = grid_sync(a))) break;
+        clock_mark(clk, PH_DOE);
         // A p = m^2 p - D_eo t and <p, A p>
         dslash_phase<P, R, EPI_AOP, Q>(a, a.fat, a.naik, a.t, a.ap, 0, st.active, a.p, nullptr, nullptr, red);
         if (!(ok = grid_sync(a))) break;
         sum_partials(a, red, n, dots);
         if (tid == 0) run_hook(HOOK_ALPHA, &st, dots, n);
         __syncthreads();
+        clock_mark(clk, PH_AOP);
         // x += alpha p; r -= alpha A p; |r|^2
         {
             double acc = 0.0;
@@ -110,6 +114,7 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         sum_partials(a, red, n, dots);
         if (tid == 0) run_hook(HOOK_DECIDE, &st, dots, n);
         __syncthreads();
+        clock_mark(clk, PH_UPDATE);
         if (st.any_update) {
             // reliable update: x_hi += x; x = 0; r = b - A x_hi in FP64 (written to r), |r|^2
             if (st.update[r]) {
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
             sum_partials(a, red, n, dots);
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
             __syncthreads();
+            clock_mark(clk, PH_RELIABLE);
         }
         // p = r + beta p
         if (st.active[r]) {
@@ -153,7 +159,9 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
             }
         }
         if (!(ok = grid_sync(a))) break;
+        clock_mark(clk, PH_PUPDATE);
     }
+    clock_store(clk, a.phase_ns);
     if (blockIdx.x == 0) {  // the final bundle state for the host
         __syncthreads();
         constexpr int WORDS = sizeof(SolverState) / sizeof(uint32_t);

@@ -1,5 +1,5 @@
-// Context, errors, link packing (row a1), vector packing and the operator entry points
-// hisq_dslash (row a2) and hisq_aop (row a3).
+// Context, errors, link packing, vector packing and the operator entry points
+// hisq_dslash and hisq_aop.
 #include <stdarg.h>
 #include <string.h>
 #include <math.h>
@@ -63,7 +63,7 @@ int ensure_scratch(hisq_ctx *ctx, size_t partial_doubles, size_t tmp_bytes) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Link packing (a1): canonical FP64 [4][V][3][3][2] -> per-parity gathered records.
+// Link packing: canonical FP64 [4][V][3][3][2] -> per-parity gathered records.
 // ------------------------------------------------------------------------------------------
 struct C64 { double re, im; };
 
@@ -317,7 +317,10 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     if (R != 1 && R != 2 && R != 4 && R != 8) R = 1;
     if (d.n % R != 0) R = 1;
     if (prec == HISQ_FP64 && R > 4) R = 4;  // FP64 kernels are built for up to four RHS per thread
-    int S = (sh.S == 2 && recon == 18 && R <= 4) ? 2 : 1;
+    // lane splits exist for 18-real Naik records: two lanes up to four RHS per thread, four up to two
+    int S = 1;
+    if (recon == 18 && sh.S == 2 && R <= 4) S = 2;
+    if (recon == 18 && sh.S == 4 && R <= 2) S = 4;
     int t = (d.n + R - 1) / R;
     // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
     // threads keep both the partial count and that block's share of the sum small

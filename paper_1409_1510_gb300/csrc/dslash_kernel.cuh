@@ -149,9 +149,53 @@ __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int n
     }
 }
 
-// The stencil of Eq. (3) at output site s (parity `parity`): accumulates into acc the products
-// of the site's 16 links (S = 1) -- or of its 8 fat (part 0) or 8 Naik links (part 1) when S = 2 --
-// with the neighbouring input vectors of the R right-hand sides r0.. that are active.
+// Neighbour `step` hops away along a direction mu known only at run time (the four-lane split
+// picks its directions by lane): the coordinate, extent and stride are selected, not indexed,
+// so nothing spills to local memory.
+__device__ __forceinline__ int neighbour_rt(const Geom &g, const SiteCoord &sc, int s, int mu, int step) {
+    const int cm = mu == 0 ? sc.c[0] : mu == 1 ? sc.c[1] : mu == 2 ? sc.c[2] : sc.c[3];
+    const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+    const int st = mu == 1 ? g.stride[1] : mu == 2 ? g.stride[2] : g.stride[3];
+    int c = cm + step;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    if (mu == 0) return sc.row_base + (c >> 1);
+    return s + (c - cm) * st;
+}
+
+// The R neighbour vectors of the active right-hand sides (zeros for the inactive ones).
+template <int P, int R, bool COHERENT>
+__device__ __forceinline__ void load_neighbours(const VecView<P> &vin, int nb, int r0, const bool act[R],
+                                                Cplx<typename Prec<P>::real> v[R][3]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        if (act[r]) {
+            load_vec<P, COHERENT>(vin, nb, r0 + r, v[r]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
+        }
+    }
+}
+
+// acc *= f
+template <typename T, int R>
+__device__ __forceinline__ void scale_acc(Cplx<T> acc[R][3], T f) {
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[r][c] = {acc[r][c].re * f, acc[r][c].im * f};
+}
+
+// The stencil of Eq. (3) at output site s (parity `parity`): writes into acc the sum of the
+// products of the site's links with the neighbouring input vectors of the R right-hand sides
+// r0.. that are active.  S = 1: all 16 links.  S = 2 (18-real Naik only): the 8 fat (part 0) or
+// the 8 Naik links (part 1).  S = 4 (18-real Naik only): part = 2 kind + half, the four links of
+// directions 2 half and 2 half + 1 of that kind.  Record slot 2 mu holds the forward link of
+// direction mu and slot 2 mu + 1 the backward one (already -U^dagger of the neighbour's link).
+// 16-bit 18-real records carry one positive float scale per (parity, site) and field; it is
+// applied to the field's summed contribution (6 R products) instead of to the 18 reals of each
+// of its links: with both fields scaled, acc = s_N (s_X / s_N sum_X + sum_N).
 template <int P, int NR, int R, int S, bool COHERENT>
 __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat_f, const LinkField &naik_f, int parity,
                                              const VecView<P> &vin, int s, int part, int r0, const bool act[R],
@@ -159,13 +203,46 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
     using real = typename Prec<P>::real;
     using FatC = LinkCodec<P, 18>;
     using NaikC = LinkCodec<P, NR>;
+    constexpr bool SCALED = (P == HISQ_FP16 || P == HISQ_BF16);  // 18-real records of 16-bit fields
     const SiteCoord sc = decode_site(g, s, parity);
+    const size_t site = (size_t)parity * g.Vh + s;
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
+    if constexpr (S == 4) {
+        static_assert(NR == 18, "the four-lane split needs identical fat and Naik encodings");
+        const bool naik_kind = (part >> 1) != 0;
+        const int half = part & 1;
+        const LinkField f = naik_kind ? naik_f : fat_f;
+        const int hop = naik_kind ? 3 : 1;
+        constexpr int GPH = 4 / FatC::G;  // groups per half record (4 links)
+#pragma unroll
+        for (int gg = 0; gg < GPH; gg++) {
+            uint32_t u[FatC::WG * 4];
+            FatC::load_group(f, parity, g.Vh, s, half * GPH + gg, u);
+#pragma unroll
+            for (int l = 0; l < FatC::G; l++) {
+                const int j = gg * FatC::G + l;  // 0..3 within the half
+                const int nb = neighbour_rt(g, sc, s, 2 * half + (j >> 1), (j & 1) ? -hop : hop);
+                Cplx<real> M[3][3];
+                FatC::decode(u, l, M);
+                Cplx<real> v[R][3];
+                load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
+                matvec_acc<real, R>(M, v, acc);
+            }
+        }
+        if constexpr (SCALED) scale_acc<real, R>(acc, (real)__ldg(f.scale + site));
+        return;
+    }
 #pragma unroll
     for (int kind = 0; kind < (S == 1 ? 2 : 1); kind++) {
         const bool naik_kind = (S == 1) ? (kind == 1) : (part == 1);
         const LinkField f = naik_kind ? naik_f : fat_f;
         const int hop = naik_kind ? 3 : 1;
         if (S == 1 && kind == 1 && NR != 18) {
+            // reconstructed Naik records are unscaled: finish the fat sum first
+            if constexpr (SCALED) scale_acc<real, R>(acc, (real)__ldg(fat_f.scale + site));
 #pragma unroll
             for (int grp = 0; grp < NaikC::GROUPS; grp++) {
                 uint32_t u[NaikC::WG * 4];
@@ -175,24 +252,18 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
                     const int slot = grp * NaikC::G + l;
                     const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -3 : 3);
                     Cplx<real> M[3][3];
-                    NaikC::decode(u, l, (real)1, M);
+                    NaikC::decode(u, l, M);
                     Cplx<real> v[R][3];
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        if (act[r]) {
-                            load_vec<P, COHERENT>(vin, nb, r0 + r, v[r]);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
-                        }
-                    }
+                    load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
                     matvec_acc<real, R>(M, v, acc);
                 }
             }
             continue;
         }
-        real lscale = (real)1;
-        if (f.scale) lscale = (real)__ldg(f.scale + (size_t)parity * g.Vh + s);
+        if constexpr (SCALED && S == 1) {
+            // between the fields: acc = (s_X / s_N) sum_X
+            if (kind == 1) scale_acc<real, R>(acc, (real)__ldg(fat_f.scale + site) / (real)__ldg(naik_f.scale + site));
+        }
 #pragma unroll
         for (int grp = 0; grp < FatC::GROUPS; grp++) {
             uint32_t u[FatC::WG * 4];
@@ -202,30 +273,27 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
                 const int slot = grp * FatC::G + l;
                 const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -hop : hop);
                 Cplx<real> M[3][3];
-                FatC::decode(u, l, lscale, M);
+                FatC::decode(u, l, M);
                 Cplx<real> v[R][3];
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    if (act[r]) {
-                        load_vec<P, COHERENT>(vin, nb, r0 + r, v[r]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; c++) v[r][c] = {0, 0};
-                    }
-                }
+                load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
                 matvec_acc<real, R>(M, v, acc);
             }
+        }
+        if constexpr (SCALED) {
+            // S = 1: after the Naik field, acc = s_N (...); S = 2: the lane's one field
+            if (S != 1 || kind == 1) scale_acc<real, R>(acc, (real)__ldg(f.scale + site));
         }
     }
 }
 
-// S = 1: one thread applies all 16 links of its site.  S = 2 (18-real Naik only): two adjacent
-// lanes share a site, lane 0 applying the 8 fat links (hops of 1) and lane 1 the 8 Naik links
-// (hops of 3) with the same instruction stream, and one shuffle adds the halves: twice the
-// threads and half the dependent-load chain per thread when there are few right-hand sides.
+// S = 1: one thread applies all 16 links of its site.  S = 2 or 4 (18-real Naik only): S adjacent
+// lanes share a site, each applying 16 / S of its links with the same instruction stream (the
+// lanes differ only in which record words, hop length and directions they use), and a shuffle
+// tree adds their parts: S times the threads and 1/S of the dependent-load chain per thread when
+// there are few right-hand sides.
 template <int P, int NR, int R, int EPI, int S>
 __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
-    static_assert(S == 1 || (S == 2 && NR == 18), "the lane split needs identical fat and Naik encodings");
+    static_assert(S == 1 || ((S == 2 || S == 4) && NR == 18), "the lane split needs identical fat and Naik encodings");
     using real = typename Prec<P>::real;
     using FatC = LinkCodec<P, 18>;
     using NaikC = LinkCodec<P, NR>;
@@ -235,7 +303,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 
     const Geom &g = a.g;
     const int tid = threadIdx.x;
-    const int part = (S == 2) ? (tid & 1) : 0;
+    const int part = tid & (S - 1);
     const int gi = (tid / S) % a.t;
     const int sl = tid / (S * a.t);
     const int r0 = gi * R;
@@ -267,15 +335,17 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
             for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
 
         if (valid) site_stencil<P, NR, R, S, false>(g, a.fat, a.naik, a.parity, vin, s, part, r0, act, acc);
-        if constexpr (S == 2) {
-            // add the fat and Naik halves; every lane of the warp takes part
+        if constexpr (S > 1) {
+            // add the lanes' parts; every lane of the warp takes part
 #pragma unroll
-            for (int r = 0; r < R; r++)
+            for (int off = 1; off < S; off <<= 1)
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    acc[r][c].re += __shfl_xor_sync(0xffffffffu, acc[r][c].re, 1);
-                    acc[r][c].im += __shfl_xor_sync(0xffffffffu, acc[r][c].im, 1);
-                }
+                for (int r = 0; r < R; r++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        acc[r][c].re += __shfl_xor_sync(0xffffffffu, acc[r][c].re, off);
+                        acc[r][c].im += __shfl_xor_sync(0xffffffffu, acc[r][c].im, off);
+                    }
         }
         if (!valid || part != 0) continue;
 

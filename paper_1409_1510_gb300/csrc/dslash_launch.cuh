@@ -36,6 +36,10 @@ inline cudaError_t launch_one(const KArgs &a, int threads, size_t smem, int num_
 template <int P, int NR, int EPI>
 inline cudaError_t launch_r(const KArgs &a, int R, int S, int threads, size_t smem, int num_sms, cudaStream_t s, int *grid) {
     if constexpr (NR == 18) {
+        if (S == 4) {
+            if (R == 1) return launch_one<P, NR, 1, EPI, 4>(a, threads, smem, num_sms, s, grid);
+            return launch_one<P, NR, 2, EPI, 4>(a, threads, smem, num_sms, s, grid);
+        }
         if (S == 2) {
             switch (R) {
             case 1: return launch_one<P, NR, 1, EPI, 2>(a, threads, smem, num_sms, s, grid);

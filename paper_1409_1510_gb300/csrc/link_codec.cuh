@@ -43,13 +43,23 @@ struct LinkCodec {
 
     // link l (0 <= l < G) of the group, times `scale` (18-real records only)
     __device__ __forceinline__ static void decode(const uint32_t *u, int l, real scale, Cplx<real> M[3][3]) {
+        decode(u, l, M);
+        if constexpr (RECON == 18) {
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int b = 0; b < 3; b++) M[a][b] = {M[a][b].re * scale, M[a][b].im * scale};
+        }
+    }
+
+    // link l (0 <= l < G) of the group as stored (16-bit 18-real records without their site scale)
+    __device__ __forceinline__ static void decode(const uint32_t *u, int l, Cplx<real> M[3][3]) {
         const int o = l * RECON;
         if constexpr (RECON == 18) {
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int b = 0; b < 3; b++)
-                    M[a][b] = {elem(u, o + 6 * a + 2 * b) * scale, elem(u, o + 6 * a + 2 * b + 1) * scale};
+                for (int b = 0; b < 3; b++) M[a][b] = {elem(u, o + 6 * a + 2 * b), elem(u, o + 6 * a + 2 * b + 1)};
         } else if constexpr (RECON == 13) {
             // rows 0, 1 of W; row 2 = conj(row0 x row1); link = c W with c = elem(12) / 24
             Cplx<real> r0[3], r1[3];

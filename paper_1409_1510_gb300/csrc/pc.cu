@@ -1,4 +1,4 @@
-// Learned gauge-covariant preconditioner (rows a7, a8): network forward, training loss and
+// Learned gauge-covariant preconditioner: network forward, training loss and
 // gradient by the project's own backward kernels, and Adam (Kingma & Ba 2014) on the GPU.
 #include <string.h>
 #include <math.h>

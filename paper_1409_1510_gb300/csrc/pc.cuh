@@ -123,7 +123,7 @@ __device__ __forceinline__ void for_each_path(const PcLayerArgs &p, int s, int k
             const int slot = grp * FatC::G + l;
             const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -1 : 1);
             Cplx<float> M[3][3];
-            FatC::decode(u, l, 1.0f, M);
+            FatC::decode(u, l, M);
             Cplx<float> h[A][3], y[A][3];
             load_channels<A>(p.in_opp, nb, k, p.K, h);
             transport<A>(M, h, y);
@@ -139,7 +139,7 @@ __device__ __forceinline__ void for_each_path(const PcLayerArgs &p, int s, int k
             const int slot = grp * NaikC::G + l;
             const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -3 : 3);
             Cplx<float> M[3][3];
-            NaikC::decode(u, l, 1.0f, M);
+            NaikC::decode(u, l, M);
             Cplx<float> h[A][3], y[A][3];
             load_channels<A>(p.in_opp, nb, k, p.K, h);
             transport<A>(M, h, y);

@@ -1,4 +1,4 @@
-// Conjugate-gradient solvers on A = m^2 - D_eo D_oe (rows a3-a6, a9): fused masked BLAS-1
+// Conjugate-gradient solvers on A = m^2 - D_eo D_oe: fused masked BLAS-1
 // kernels with FP64 bundle reductions, device-side per-right-hand-side control (hooks), FP64
 // reliable updates, and two drivers: host-driven iterations (residual flags read back every
 // check_every iterations, as the per-iteration residual transfer of Sec. 2) and a single
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) cg_xhi_kernel(BlasArgs a) {
     }
 }
 
-// ---- flexible CG (row a9) -------------------------------------------------------------------
+// ---- flexible CG -------------------------------------------------------------------
 // zz = z (network output) or r (after a stall fallback); dots <r - r_old, zz> -> HOOK_FCG_BETA
 template <int P>
 __global__ void __launch_bounds__(256) fcg_beta_kernel(BlasArgs a) {
@@ -352,6 +352,7 @@ struct Workspace {
     double *dots = nullptr;
     unsigned int *bar = nullptr;   // persistent solve: grid-barrier arrivals and generation
     int *err = nullptr;            // persistent solve: a barrier wait ran out
+    unsigned long long *phase_ns = nullptr;  // persistent solve: per-phase time (time_kernels)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     GraphCache gc;
 };
@@ -385,7 +386,8 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
             cudaMalloc(&w->counter, sizeof(unsigned int) * 4) != cudaSuccess ||
             cudaMalloc(&w->dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) != cudaSuccess ||
             cudaMalloc(&w->bar, sizeof(unsigned int) * 4) != cudaSuccess ||
-            cudaMalloc(&w->err, sizeof(int) * 4) != cudaSuccess)
+            cudaMalloc(&w->err, sizeof(int) * 4) != cudaSuccess ||
+            cudaMalloc(&w->phase_ns, sizeof(unsigned long long) * 8) != cudaSuccess)
             return set_error(HISQ_ERR_NOMEM, "solver workspace allocation failed");
         w->partials_cap = pcap;
         cudaMemset(w->counter, 0, sizeof(unsigned int) * 4);
@@ -436,6 +438,7 @@ void free_workspace(hisq_ctx *ctx) {
     if (w->dots) cudaFree(w->dots);
     if (w->bar) cudaFree(w->bar);
     if (w->err) cudaFree(w->err);
+    if (w->phase_ns) cudaFree(w->phase_ns);
     if (w->ev0) cudaEventDestroy(w->ev0);
     if (w->ev1) cudaEventDestroy(w->ev1);
     delete w;
@@ -457,6 +460,8 @@ struct Solve {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *events64;  // FP64 Dslash
     const hisq_pc *pc;                                           // flexible CG when set
     bool persistent = false;                                     // solved by the persistent kernel
+    bool pers_timing = false;        // time the persistent kernel (CUDA events) and its phases
+    hisq_solve_stats *stats = nullptr;
 };
 
 static BlasArgs blas_args(const Solve &S) {
@@ -811,17 +816,33 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     HISQ_CHECK(pack_vectors(S.ctx, w->canon, w->b_hi, S.n, HISQ_FP64, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->bar, 0, sizeof(unsigned int) * 4, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int) * 4, S.st));
+    if (S.pers_timing) {
+        a.phase_ns = w->phase_ns;
+        HISQ_CUDA(cudaMemsetAsync(w->phase_ns, 0, sizeof(unsigned long long) * 8, S.st));
+        HISQ_CUDA(cudaEventRecord(w->ev0, S.st));
+    }
     cudaError_t e = persistent_launch(S.prec, a, R, grid, smem, S.st);
     if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
         cudaGetLastError();
         return HISQ_OK;  // not co-resident here: the graph driver takes the bundle
     }
     if (e != cudaSuccess) return set_error(HISQ_ERR_CUDA, "persistent solve launch failed: %s", cudaGetErrorString(e));
+    if (S.pers_timing) HISQ_CUDA(cudaEventRecord(w->ev1, S.st));
     int err_h = 0;
+    unsigned long long ph[8] = {0};
     HISQ_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(SolverState), cudaMemcpyDeviceToHost, S.st));
     HISQ_CUDA(cudaMemcpyAsync(&err_h, w->err, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    if (S.pers_timing) HISQ_CUDA(cudaMemcpyAsync(ph, w->phase_ns, sizeof(ph), cudaMemcpyDeviceToHost, S.st));
     HISQ_CUDA(cudaStreamSynchronize(S.st));
     if (err_h) return set_error(HISQ_ERR_TIMEOUT, "a grid barrier of the persistent solve ran out of its wait budget");
+    if (S.pers_timing && S.stats) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, w->ev0, w->ev1) == cudaSuccess) {
+            S.stats->solve_kernel_ms += ms;
+            S.stats->solve_kernel_launches++;
+        }
+        for (int i = 0; i < PERS_PHASES; i++) S.stats->phase_ms[i] += (double)ph[i] * 1e-6;
+    }
     *done = true;
     return HISQ_OK;
 }
@@ -948,6 +969,8 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
         int n = std::min(bundle, nrhs - k0);
         Solve S{ctx, w, fat, naik, n, prec, mass, ctx->stream, P.time_kernels != 0 && !P.use_graph, &events, &events64,
                 P.pc};
+        S.pers_timing = P.time_kernels != 0 && P.use_graph == 2;
+        S.stats = &stats;
         // tune (outside any capture) before the first use of this shape
         if (P.autotune) {
             tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64);

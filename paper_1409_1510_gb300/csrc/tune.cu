@@ -1,4 +1,4 @@
-// Launch-shape autotuner for the Dslash (row a6): for a given precision, Naik reconstruction
+// Launch-shape autotuner for the Dslash: for a given precision, Naik reconstruction
 // and bundle size it times every candidate (right-hand sides per thread R dividing n, threads
 // per block) with CUDA events on scratch bundles and caches the fastest in the context.
 #include <string.h>
@@ -71,8 +71,8 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     for (int R : Rs) {
         if (n % R != 0) continue;
         if (prec == HISQ_FP64 && R > 4) continue;
-        for (int S = 1; S <= 2; S++) {
-        if (S == 2 && (recon != 18 || R > 4)) continue;
+        for (int S = 1; S <= 4; S *= 2) {
+        if (S > 1 && (recon != 18 || R > 8 / S)) continue;
         for (int T : Ts) {
             LaunchShape sh{R, T, S};
             float ms = 0;
@@ -147,8 +147,11 @@ extern "C" int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_
     if ((R != 1 && R != 2 && R != 4 && R != 8) || nrhs % R != 0 || (prec == HISQ_FP64 && R > 4))
         return set_error(HISQ_ERR_ARG, "rhs_per_thread %d is not available for nrhs %d", R, nrhs);
     if (block_threads < 32 || block_threads > 256) return set_error(HISQ_ERR_ARG, "block_threads must be in 32..256");
-    if (lanes_per_site != 1 && !(lanes_per_site == 2 && recon == 18 && R <= 4))
-        return set_error(HISQ_ERR_ARG, "lanes_per_site must be 1, or 2 with 18-real Naik links and rhs_per_thread <= 4");
+    if (lanes_per_site != 1 && !(lanes_per_site == 2 && recon == 18 && R <= 4) &&
+        !(lanes_per_site == 4 && recon == 18 && R <= 2))
+        return set_error(HISQ_ERR_ARG,
+                         "lanes_per_site must be 1, 2 (18-real Naik links, rhs_per_thread <= 4) or 4 (18-real Naik "
+                         "links, rhs_per_thread <= 2)");
     ctx->tuned[TuneKey{prec, recon, nrhs, 0}] = LaunchShape{R, block_threads, lanes_per_site};
     ctx->tune_generation++;
     return HISQ_OK;

@@ -43,7 +43,8 @@ class hisq_solve_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("dslash_ms", ctypes.c_double),
                 ("dslash_launches", ctypes.c_int), ("dslash64_ms", ctypes.c_double),
                 ("dslash64_launches", ctypes.c_int), ("flops", ctypes.c_double),
-                ("kernel_launches", ctypes.c_long)]
+                ("kernel_launches", ctypes.c_long), ("solve_kernel_ms", ctypes.c_double),
+                ("solve_kernel_launches", ctypes.c_int), ("phase_ms", ctypes.c_double * 5)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -1,4 +1,4 @@
-"""Dslash (rows a1-a3) on the GPU through the C ABI, element by element against the FP64 oracle."""
+"""Link packing, Dslash (Eq. (3), (4)) and A-operator on the GPU through the C ABI, element by element against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -41,8 +41,8 @@ def test_every_launch_shape(prec):
         for R in (1, 2, 4, 8):
             if prec == 0 and R == 8:
                 continue
-            for S in (1, 2):
-                if S == 2 and R == 8:
+            for S in (1, 2, 4):
+                if S * R > 8:
                     continue
                 for threads in (32, 96, 256):
                     g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads, S)
@@ -51,14 +51,15 @@ def test_every_launch_shape(prec):
                     assert rel_err(g.unpack(vout, n), want) <= PREC_TOL[prec], (R, S, threads)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n", [1, 3])
 def test_lane_split_with_fused_epilogues(prec, n):
-    """The two-lane (fat / Naik) split with the A-operator epilogue and its fused dot."""
+    """The two-lane (fat / Naik) and four-lane (two directions of one kind) splits with the
+    A-operator epilogue and its fused dot."""
     mass = 0.2
     with gpu(DIMS, prec, 18) as g:
         v = _rhs(g.lat, n, 80)
-        for S in (1, 2):
+        for S in (1, 2, 4):
             g.hisq.hisq_set_launch_shape(prec, 18, n, 1, 128, S)
             vin, vout = g.pack(v), g.bundle(n)
             pap = np.zeros(n)
@@ -88,7 +89,7 @@ def test_dslash_zero_input_gives_zero():
 
 @pytest.mark.parametrize("prec,recon", CASES)
 def test_links_export_matches_gathered_links(prec, recon):
-    """Row a1: the packed links decode to X_{x,mu} and -X^dag_{x-mu,mu} (N with 3 hops) of the
+    """The packed links decode to X_{x,mu} and -X^dag_{x-mu,mu} (N with 3 hops) of the
     canonical input, within the storage precision."""
     dims = (8, 4, 6, 4)
     with gpu(dims, prec, recon) as g:
@@ -118,7 +119,7 @@ def test_links_export_matches_gathered_links(prec, recon):
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n", [1, 5, 16])
 def test_aop_and_fused_dot(prec, n):
-    """Row a3: A p = m^2 p - D_eo D_oe p with the fused <p, A p> in FP64."""
+    """A p = m^2 p - D_eo D_oe p with the fused <p, A p> in FP64."""
     mass = 0.1
     with gpu(DIMS, prec, 18) as g:
         v = _rhs(g.lat, n, 7)
@@ -142,3 +143,14 @@ def test_full_size_dslash_32c8(prec):
             vin, vout = g.pack(v), g.bundle(n)
             g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 0)
             assert rel_err(g.unpack(vout, n), g.oracle.dslash_eo(v, 0)) <= PREC_TOL[prec]
+
+
+def test_launch_shape_validation():
+    """Lane splits exist only for 18-real Naik records and few right-hand sides per thread."""
+    from paper_1409_1510_gb300.hisq import HisqError
+    with gpu(DIMS, 1, 18) as g:
+        h = g.hisq
+        h.hisq_set_launch_shape(1, 18, 4, 2, 128, 4)
+        for bad in ((1, 18, 4, 4, 128, 4), (1, 13, 4, 1, 128, 2), (1, 18, 4, 1, 128, 3)):
+            with pytest.raises(HisqError):
+                h.hisq_set_launch_shape(*bad)

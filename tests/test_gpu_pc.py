@@ -1,4 +1,4 @@
-"""Learned preconditioner (rows a7-a9) on the GPU through the C ABI against the FP64 oracle:
+"""Learned gauge-covariant preconditioner (forward, training, flexible CG) on the GPU through the C ABI against the FP64 oracle:
 network forward, training loss and gradient of the project's backward kernels, Adam, training,
 and flexible CG with its stall fallback."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""CG solves (rows a4-a6) on the GPU through the C ABI; every solution is judged by the FP64
+"""Mixed-precision, batched CG solves on the GPU through the C ABI; every solution is judged by the FP64
 oracle's true residual |b - A x| / |b|."""
 import numpy as np
 import pytest
@@ -25,7 +25,7 @@ def _solve(g, rhs, mass, **params):
     return np.stack(xs), stats, iters, res
 
 
-def test_config0_plain_fp64():
+def test_plain_fp64_cg_8c4():
     """8^3 x 4, one RHS, FP64 everywhere, m = 0.1, to true residual 1e-10; iteration count of
     the textbook oracle CG within a few."""
     dims = (8, 8, 8, 4)
@@ -169,3 +169,17 @@ def test_persistent_barrier_timeout_is_reported_and_context_survives():
         assert rc == -6
         x, stats, iters, res = _solve(g, [b], 0.1, inner_prec=1, use_graph=2)
         assert g.oracle.true_residual(b, x[0], 0.1)[0] <= TOL * SLACK
+
+
+def test_persistent_kernel_timing_and_phases():
+    """time_kernels with the persistent driver: one CUDA-event-timed kernel per bundle, and the
+    per-phase times from inside the kernel fill most of it without exceeding it."""
+    dims = (8, 10, 8, 6)
+    with gpu(dims, 2) as g:
+        rhs = [hi.gaussian_rhs(g.lat, 70 + k) for k in range(3)]
+        x, s, iters, _ = _solve(g, rhs, 0.05, inner_prec=2, use_graph=2, time_kernels=1, bundle=2)
+        assert s.bundles == 2 and s.solve_kernel_launches == 2 and s.solve_kernel_ms > 0
+        ph = list(s.phase_ms)
+        assert all(v >= 0 for v in ph) and ph[0] > 0 and ph[1] > 0 and ph[3] > 0
+        assert sum(ph) <= s.solve_kernel_ms * 1.01
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x, 0.05) <= TOL * SLACK)
