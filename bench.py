@@ -29,6 +29,8 @@ if ROOT not in sys.path:
 METRIC = "HISQ Dslash GFlop/s & HBM GB/s; CG s/RHS to res 1e-10 vs plain FP64 CG"
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 TOL = 1e-10
+DEFAULT_DIMS = "32,32,32,8"
+DEFAULT_MASS = 0.01
 
 
 def parse():
@@ -38,15 +40,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", default="fp16", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--dims", default="32,32,32,8")
-    ap.add_argument("--mass", type=float, default=0.01)
+    ap.add_argument("--dims", default=DEFAULT_DIMS)
+    ap.add_argument("--mass", type=float, default=DEFAULT_MASS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cg", choices=["cg", "sweep", "learned"],
+    ap.add_argument("--mode", default="cg", choices=["cg", "sweep", "learned", "batch", "production"],
                     help="cg: the benchmark line; sweep: Dslash throughput against the number of "
-                         "right-hand sides; learned: the learned-preconditioner workload")
+                         "right-hand sides; learned: the learned-preconditioner workload (32^3 x 8); "
+                         "batch: bundles with uneven convergence (48^3 x 12); production: a sweep of "
+                         "Z2-noise right-hand sides (64^3 x 16)")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--test-rhs", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--nrhs", type=int, default=1500, help="production: right-hand sides in the sweep")
+    ap.add_argument("--pc", action="store_true", help="production: also train and apply the network")
     return ap.parse_args()
 
 
@@ -332,7 +338,7 @@ def run_ours(args, rank, world, local_rank, dist):
     ds_gbs = ds_bytes / ((ph[0] + ph[1]) / 1e3) / 1e9 if ph[0] + ph[1] > 0 else None
     rel_gflops = ups * 2 * acc.DSLASH_FLOPS_PER_SITE * Vh / (ph[3] / 1e3) / 1e9 if ph[3] > 0 else None
     phases = {"ms_per_launch": {name: ph[i] / max(k_n, 1) for i, name in
-                                enumerate(("dslash_doe", "dslash_aop_dot", "xr_update", "fp64_reliable", "p_update"))},
+                                enumerate(("dslash_doe", "dslash_aop_dot", "pxr_update", "fp64_reliable"))},
               "dslash_phases_gbs": ds_gbs, "dslash_phases_frac": ds_gbs / hbm_peak if ds_gbs else None,
               "fp64_reliable_gflops": rel_gflops,
               "fp64_reliable_share": ph[3] / k_ms if k_ms > 0 else None,
@@ -505,32 +511,19 @@ def run_sweep(args):
     hisq.hisq_finalize()
 
 
-def run_learned(args):
-    """Learned-preconditioner workload: (r, e) pairs from plain CG iterates on the same gauge
-    field, training on the GPU, then flexible CG against plain CG on fresh right-hand sides."""
-    import torch
-    import hisq_inputs as hi
-    from paper_1409_1510_gb300 import hisq
-    dims, _ = workload(args)
-    mass, tol = args.mass, TOL
-    lat = hi.Lattice(dims)
-    X, N = hi.fat_links(lat), hi.naik_links(lat)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
-    hisq.hisq_init(dims, 0, stream)
-    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
-    fat = hisq.hisq_links_create(d64(X), False, 1, 18)
-    naik = hisq.hisq_links_create(d64(N), True, 1, 18)
+def make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, want):
+    """(r, e) training pairs from plain FP32 CG on this gauge field: 16 right-hand sides at a time
+    are solved to 1e-10 (x*), then re-solved for k iterations (x_k) at 25 values of k up to 80% of
+    the iteration count; e = x* - x_k, r = b - A x_k (so A e = r).  Returns packed FP32 bundles of
+    16 pairs (r and e) and the number of pairs."""
     vh = lat.half_volume
+    dev = torch.device("cuda", 0)
     p = hisq.hisq_default_solver_params()
     p.inner_prec = 1
-    hisq.hisq_set_solver_params(p)
-    # pairs: 16 right-hand sides at a time, x* to 1e-10, then x_k after k iterations
-    t0 = time.perf_counter()
     per_rhs = 25
-    nrhs = (args.pairs + per_rhs - 1) // per_rhs
+    nrhs = (want + per_rhs - 1) // per_rhs
     bsz = hisq.hisq_vector_bytes(1, 16)
-    nb = (args.pairs + 15) // 16
+    nb = (want + 15) // 16
     rbuf = torch.empty(nb * bsz, dtype=torch.uint8, device=dev)
     ebuf = torch.empty_like(rbuf)
     pending_r, pending_e, filled = [], [], 0
@@ -540,14 +533,15 @@ def run_learned(args):
         bs = [d64(hi.gaussian_rhs(lat, 7000 + j)) for j in range(j0, min(nrhs, j0 + 16))]
         xs = [torch.zeros_like(b) for b in bs]
         p.max_iter = 20000
+        p.bundle = len(bs)
         hisq.hisq_set_solver_params(p)
-        hisq.hisq_cg_solve(fat, naik, bs, xs, mass, tol)
+        hisq.hisq_cg_solve(fat, naik, bs, xs, mass, TOL)
         its = hisq.hisq_last_stats().max_iterations
         for k in np.linspace(2, max(3, int(0.8 * its)), per_rhs).astype(int):
             p.max_iter = int(k)
             hisq.hisq_set_solver_params(p)
             xk = [torch.zeros_like(b) for b in bs]
-            hisq.hisq_cg_solve(fat, naik, bs, xk, mass, tol, raise_on_error=False)
+            hisq.hisq_cg_solve(fat, naik, bs, xk, mass, TOL, raise_on_error=False)
             # r_k = b - A x_k on the GPU (A in FP32 through the library)
             xin = torch.empty(hisq.hisq_vector_bytes(1, len(bs)), dtype=torch.uint8, device=dev)
             ax = torch.empty_like(xin)
@@ -556,7 +550,7 @@ def run_learned(args):
             axc = torch.empty((len(bs), vh, 3, 2), dtype=torch.float64, device=dev)
             hisq.hisq_unpack(ax, axc, len(bs), 1)
             for q in range(len(bs)):
-                if done >= args.pairs:
+                if done >= want:
                     break
                 pending_r.append(bs[q].view(vh, 3, 2) - axc[q])
                 pending_e.append(xs[q].view(vh, 3, 2) - xk[q].view(vh, 3, 2))
@@ -566,40 +560,55 @@ def run_learned(args):
                     hisq.hisq_pack(canon(pending_e), ebuf[filled * bsz:(filled + 1) * bsz], 16, 1)
                     filled += 1
                     pending_r, pending_e = [], []
-    pairs = filled * 16
-    t_pairs = time.perf_counter() - t0
-    # training from the identity plus a small random perturbation (the identity is a saddle point)
+    return rbuf, ebuf, filled * 16
+
+
+def train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, epochs, hist=None):
+    """Adam on the GPU from the identity plus a 2% random perturbation (the identity is a saddle
+    point); returns the preconditioner handle."""
     rng = np.random.default_rng(0)
     w0 = np.zeros(408, complex)
     w0[[0, 68, 340]] = 1.0
     w0 += 0.02 * (rng.standard_normal(408) + 1j * rng.standard_normal(408))
     pc = hisq.hisq_pc_create(np.ascontiguousarray(w0).view(np.float64))
+    if hist is None:
+        hist = np.zeros(epochs)
+    hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, npairs, 16, epochs, 5e-3, hist)
+    torch.cuda.synchronize()
+    return pc
+
+
+def run_learned(args):
+    """Learned-preconditioner workload: (r, e) pairs from plain CG iterates on the same gauge
+    field, training on the GPU, then flexible CG against plain CG on fresh right-hand sides."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims, _ = workload(args)
+    mass = args.mass
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    hisq.hisq_init(dims, 0, torch.cuda.current_stream())
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    fat = hisq.hisq_links_create(d64(X), False, 1, 18)
+    naik = hisq.hisq_links_create(d64(N), True, 1, 18)
+    t0 = time.perf_counter()
+    rbuf, ebuf, pairs = make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, args.pairs)
+    t_pairs = time.perf_counter() - t0
     hist = np.zeros(args.epochs)
     t0 = time.perf_counter()
-    hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, pairs, 16, args.epochs, 5e-3, hist)
-    torch.cuda.synchronize()
+    pc = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, pairs, args.epochs, hist)
     t_train = time.perf_counter() - t0
     # fresh right-hand sides: plain CG against flexible CG with the network (both FP32 inner,
     # FP64 reliable updates, true residual 1e-10 judged in FP64)
     tests = [d64(hi.gaussian_rhs(lat, 9000 + k)) for k in range(args.test_rhs)]
     out = {}
     for name, handle in (("cg", None), ("fcg_learned", pc)):
-        p = hisq.hisq_default_solver_params()
-        p.inner_prec = 1
-        p.pc = handle.value if handle is not None else None
-        p.bundle = 16
-        hisq.hisq_set_solver_params(p)
-        xs = [torch.zeros_like(b) for b in tests]
-        hisq.hisq_cg_solve(fat, naik, tests[:16], xs[:16], mass, tol)  # warm-up / capture
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hisq.hisq_cg_solve(fat, naik, tests, xs, mass, tol)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        iters = np.zeros(len(tests), dtype=np.int32)
-        res = np.zeros(len(tests))
-        st = hisq.hisq_last_stats(iters, res)
-        out[name] = {"s_per_rhs": el / len(tests), "mean_iterations": float(iters.mean()),
+        hv = handle.value if handle is not None else None
+        _solve_set(hisq, torch, fat, naik, tests[:16], mass, inner_prec=1, bundle=16, pc=hv)  # warm-up
+        sec, st, iters, res = _solve_set(hisq, torch, fat, naik, tests, mass, inner_prec=1, bundle=16, pc=hv)
+        out[name] = {"s_per_rhs": sec / len(tests), "mean_iterations": float(iters.mean()),
                      "max_true_residual": float(res.max()), "converged": st.converged,
                      "fallbacks": st.fallbacks}
     line = {"mode": "learned", "lattice": dims, "mass": mass, "pairs": pairs, "pair_seconds": t_pairs,
@@ -611,6 +620,165 @@ def run_learned(args):
     hisq.hisq_finalize()
 
 
+def _solve_set(hisq, torch, fat, naik, bs, mass, **params):
+    """Solve the right-hand sides bs (device canonical) with the given solver parameters; returns
+    (seconds by CUDA events, stats, iterations, true residuals)."""
+    p = hisq.hisq_default_solver_params()
+    for k, v in params.items():
+        setattr(p, k, v)
+    hisq.hisq_set_solver_params(p)
+    xs = [torch.zeros_like(b) for b in bs]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hisq.hisq_cg_solve(fat, naik, bs, xs, mass, TOL)
+    e1.record(stream)
+    e1.synchronize()
+    iters = np.zeros(len(bs), dtype=np.int32)
+    res = np.zeros(len(bs))
+    st = hisq.hisq_last_stats(iters, res)
+    return e0.elapsed_time(e1) / 1e3, st, iters, res
+
+
+def run_batch(args):
+    """Batching form on 48^3 x 12, m = 0.002, FP32 storage: 16 Gaussian right-hand sides with
+    norms log-uniform in 1e-3..1e3 and spectral shaping (b_k = s_k A^{q_k} g_k / |.|, q_k = k mod 3,
+    A applied in FP64 by the library), solved in bundles of n = 1, 2, 4, 8, 12, 16 by the persistent
+    kernel and by the captured CUDA graph, and with the bundle size chosen by the autotuner."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims = tuple(int(x) for x in args.dims.split(",")) if args.dims != DEFAULT_DIMS else (48, 48, 48, 12)
+    mass = args.mass if args.mass != DEFAULT_MASS else 0.002
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    hisq.hisq_init(dims, 0, torch.cuda.current_stream())
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    vh, nrhs = lat.half_volume, 16
+    # the shaped right-hand sides (FP64 A through the library)
+    f64 = hisq.hisq_links_create(d64(X), False, 0, 18)
+    n64 = hisq.hisq_links_create(d64(N), True, 0, 18)
+    scales = 10.0 ** np.random.default_rng(2000).uniform(-3.0, 3.0, nrhs)
+    bs = []
+    vin = torch.empty(hisq.hisq_vector_bytes(0, 1), dtype=torch.uint8, device=dev)
+    vout = torch.empty_like(vin)
+    for k in range(nrhs):
+        g = d64(hi.gaussian_rhs(lat, 2000 + k))
+        for _ in range(k % 3):
+            hisq.hisq_pack(g, vin, 1, 0)
+            hisq.hisq_aop(f64, n64, mass, vin, vout, 1)
+            g = torch.empty_like(g)
+            hisq.hisq_unpack(vout, g, 1, 0)
+        bs.append((g * (scales[k] / torch.linalg.vector_norm(g))).contiguous())
+    hisq.hisq_links_destroy(f64)
+    hisq.hisq_links_destroy(n64)
+    fat = hisq.hisq_links_create(d64(X), False, 1, 18)
+    naik = hisq.hisq_links_create(d64(N), True, 1, 18)
+    rows = []
+    for n in (1, 2, 4, 8, 12, 16):
+        row = {"bundle": n}
+        for name, driver in (("persistent", 2), ("graph", 1)):
+            _solve_set(hisq, torch, fat, naik, bs[:n], mass, inner_prec=1, bundle=n, use_graph=driver)  # warm-up
+            sec, st, iters, res = _solve_set(hisq, torch, fat, naik, bs, mass, inner_prec=1, bundle=n, use_graph=driver)
+            row[name] = {"s_per_rhs": sec / nrhs, "iterations_min": int(iters.min()), "iterations_max": int(iters.max()),
+                         "bundle_iterations": int(st.bundle_iterations), "converged": int(st.converged),
+                         "max_true_residual": float(res.max())}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    sec, st, iters, res = _solve_set(hisq, torch, fat, naik, bs, mass, inner_prec=1, bundle=0)
+    auto = {"bundle_chosen": int(st.bundle_size), "s_per_rhs": sec / nrhs, "converged": int(st.converged),
+            "max_true_residual": float(res.max())}
+    line = {"mode": "batch", "lattice": list(dims), "mass": mass, "nrhs": nrhs, "storage": "fp32",
+            "rhs": "Gaussian, norms log-uniform 1e-3..1e3, spectral shaping A^(k mod 3)",
+            "bundles": rows, "autotuned": auto,
+            "speedup_16_vs_1": rows[0]["persistent"]["s_per_rhs"] / rows[-1]["persistent"]["s_per_rhs"]}
+    print(json.dumps(line), flush=True)
+    hisq.hisq_finalize()
+
+
+def run_production(args):
+    """Production-shaped sweep on 64^3 x 16, m = 0.002: args.nrhs Z2-noise right-hand sides,
+    FP16 storage with FP64 reliable updates, bundle size from the autotuner, every right-hand side
+    to the FP64 true residual 1e-10; the Dslash phases' HBM rate from the persistent kernel's
+    phase clock.  With --pc, the network is trained on this gauge field (FP32) and flexible CG is
+    compared with plain FP32 CG on a sample of the right-hand sides."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import accounting as acc
+    from paper_1409_1510_gb300 import hisq
+    dims = tuple(int(x) for x in args.dims.split(",")) if args.dims != DEFAULT_DIMS else (64, 64, 64, 16)
+    mass = args.mass if args.mass != DEFAULT_MASS else 0.002
+    lat = hi.Lattice(dims)
+    t0 = time.perf_counter()
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    t_fields = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    hisq.hisq_init(dims, 0, torch.cuda.current_stream())
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    fat = hisq.hisq_links_create(d64(X), False, 2, 18)
+    naik = hisq.hisq_links_create(d64(N), True, 2, 18)
+    vh = lat.half_volume
+    hbm_peak, _ = peaks()
+    chunk = 96  # right-hand sides per call (the library splits them into tuned bundles)
+    _solve_set(hisq, torch, fat, naik, [d64(hi.z2_rhs(lat, 50000 + k)) for k in range(16)], mass,
+               inner_prec=2, bundle=0)  # warm-up: tuning and first launches
+    tot_s, its, ups, conv, worst, ph, kms, bits, nb = 0.0, [], 0, 0, 0.0, np.zeros(5), 0.0, 0, 0
+    t_wall = time.perf_counter()
+    for k0 in range(0, args.nrhs, chunk):
+        bs = [d64(hi.z2_rhs(lat, 60000 + k)) for k in range(k0, min(args.nrhs, k0 + chunk))]
+        sec, st, iters, res = _solve_set(hisq, torch, fat, naik, bs, mass, inner_prec=2, bundle=0, time_kernels=1)
+        tot_s += sec
+        its += iters.tolist()
+        ups += st.reliable_updates
+        conv += st.converged
+        worst = max(worst, float(res.max()))
+        ph += np.array(list(st.phase_ms))
+        kms += st.solve_kernel_ms
+        bits += st.bundle_iterations
+        nb = st.bundle_size
+    t_wall = time.perf_counter() - t_wall
+    P_b = acc.VECTOR_BYTES[2]
+    ds_bytes = bits * (2 * acc.LINK_BYTES_18[2] + 5 * P_b * nb) * vh
+    line = {"mode": "production", "lattice": list(dims), "mass": mass, "nrhs": args.nrhs, "storage": "fp16",
+            "bundle_chosen": nb, "sweep_seconds_gpu": tot_s, "sweep_seconds_wall": t_wall,
+            "s_per_rhs": tot_s / args.nrhs, "converged": conv, "max_true_residual": worst,
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+            "reliable_updates": int(ups),
+            "dslash_phases_gbs": ds_bytes / (ph[0] + ph[1]) * 1e3 / 1e9 if ph[0] + ph[1] > 0 else None,
+            "fp64_reliable_share": ph[3] / kms if kms > 0 else None, "field_generation_s": t_fields}
+    line["dslash_phases_frac"] = line["dslash_phases_gbs"] / hbm_peak if line["dslash_phases_gbs"] else None
+    if args.pc:
+        line["learned"] = production_pc(args, hisq, torch, hi, lat, X, N, mass, d64)
+    print(json.dumps(line), flush=True)
+    hisq.hisq_finalize()
+
+
+def production_pc(args, hisq, torch, hi, lat, X, N, mass, d64):
+    """Train the network on (r, e) pairs of this gauge field (FP32 links) and compare flexible CG
+    with plain CG on a sample of Z2 right-hand sides."""
+    fat = hisq.hisq_links_create(d64(X), False, 1, 18)
+    naik = hisq.hisq_links_create(d64(N), True, 1, 18)
+    pairs = make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, args.pairs)
+    rbuf, ebuf, npairs = pairs
+    pc = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, args.epochs)
+    sample = [d64(hi.z2_rhs(lat, 60000 + k)) for k in range(args.test_rhs)]
+    out = {"pairs": npairs, "epochs": args.epochs}
+    for name, handle in (("cg", None), ("fcg_learned", pc)):
+        _solve_set(hisq, torch, fat, naik, sample[:16], mass, inner_prec=1, bundle=16,
+                   pc=handle.value if handle is not None else None)
+        sec, st, iters, res = _solve_set(hisq, torch, fat, naik, sample, mass, inner_prec=1, bundle=16,
+                                         pc=handle.value if handle is not None else None)
+        out[name] = {"s_per_rhs": sec / len(sample), "mean_iterations": float(iters.mean()),
+                     "max_true_residual": float(res.max()), "converged": int(st.converged),
+                     "fallbacks": int(st.fallbacks)}
+    hisq.hisq_pc_destroy(pc)
+    hisq.hisq_links_destroy(fat)
+    hisq.hisq_links_destroy(naik)
+    return out
+
+
 def main():
     args = parse()
     if args.mode == "sweep":
@@ -618,6 +786,12 @@ def main():
         return
     if args.mode == "learned":
         run_learned(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
+        return
+    if args.mode == "production":
+        run_production(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

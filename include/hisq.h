@@ -159,7 +159,10 @@ typedef struct {
                              reliable updates (needs links packed in that precision) */
     double delta;         /* reliable update when |r| < delta * |r at the last update| (0.1) */
     int max_iter;         /* per right-hand side (default 20000) */
-    int bundle;           /* right-hand sides per bundle, 1..HISQ_MAX_BUNDLE; 0 = autotuned */
+    int bundle;           /* right-hand sides per bundle, 1..HISQ_MAX_BUNDLE; 0 (default) = the
+                             autotuner's choice among 1, 2, 4, 8, 12, 16 and min(nrhs, 16): the
+                             split of nrhs into bundles with the least summed tuned Dslash time
+                             (min(nrhs, 16) when autotune is 0) */
     int use_graph;        /* driver of a bundle: 0 host-driven iterations; 1 one captured CUDA
                              graph with device-side control flow (WHILE/IF conditional nodes);
                              2 (default) one persistent cooperative kernel for the whole solve,
@@ -175,6 +178,9 @@ typedef struct {
     int debug_barrier_timeout; /* test hook for failure detection: 1 makes every grid barrier of
                              the persistent solve wait for one block more than it launches, so the
                              bounded waits run out and the solve returns HISQ_ERR_TIMEOUT */
+    int persistent_threads; /* block size of the persistent solve kernel: 0 = 512; otherwise a
+                             multiple of 32 up to 1024 (one right-hand side per thread) or 512;
+                             the grid is every block that fits on the GPU at once */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);
@@ -212,9 +218,10 @@ typedef struct {
                                  time_kernels = 1; CUDA events on the solve's stream) */
     int solve_kernel_launches;
     double phase_ms[5];       /* inside those kernels, block 0's time from one grid barrier to the
-                                 next, summed per phase: [0] D_oe p, [1] A p = m^2 p - D_eo t with
-                                 <p, A p>, [2] x, r update with |r|^2, [3] FP64 residual
-                                 recomputations, [4] p = r + beta p (each with its scalar step) */
+                                 next, summed per phase (each with its scalar step): [0] D_oe p,
+                                 [1] A p = m^2 p - D_eo t with <p, A p>, [2] the p, x, r update
+                                 with |r|^2, [3] FP64 residual recomputations, [4] unused (0: the
+                                 direction p = r + beta p is formed inside phases 0-2) */
 } hisq_solve_stats;
 
 /* Statistics of the calling thread's last hisq_cg_solve.  iterations (int[nrhs]) and
@@ -256,15 +263,33 @@ int hisq_pc_get_weights(const hisq_pc *pc, double *weights /* host */);
 int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
                   const void *in, void *out, int nrhs);
 
-/* out = M_H(in), M_H = (M + M^dag) / 2 the Hermitian part of the network (M^dag applies the adjoint
- * layers in reverse order).  This is the preconditioner hisq_cg_solve applies in flexible CG: a
- * trained M is not Hermitian, and its Hermitian part keeps the short CG recurrence valid. */
+/* out = M^dag(in): the adjoint network (the adjoint layers in reverse order). */
+int hisq_pc_apply_adjoint(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                          const void *in, void *out, int nrhs);
+
+/* out = M_H(in), M_H = (M + M^dag) / 2, the Hermitian part of the network. */
 int hisq_pc_apply_hermitian(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
                             const void *in, void *out, int nrhs);
 
+/* out = M^dag M (in), the normal form of the network: Hermitian and positive semi-definite for
+ * any weights. */
+int hisq_pc_apply_normal(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                         const void *in, void *out, int nrhs);
+
+/* Which operator of the network the handle stands for, in training (hisq_pc_loss_grad,
+ * hisq_pc_train) and as the preconditioner of hisq_cg_solve's flexible CG.  A trained M is not
+ * Hermitian, and flexible CG truncated to one previous direction then loses conjugacy; both
+ * forms keep the short recurrence of preconditioned CG:
+ *   HISQ_PC_NORMAL (default)  P = M^dag M, positive semi-definite by construction;
+ *   HISQ_PC_HERMITIAN_PART    P = (M + M^dag) / 2, trained as M itself. */
+#define HISQ_PC_NORMAL 1
+#define HISQ_PC_HERMITIAN_PART 0
+int hisq_pc_set_form(hisq_pc *pc, int form);
+
 /* Training loss over K pairs (r_k, e_k) with A e_k = r_k (residual and error of a CG iterate):
- *   loss = (1/K) sum_k |A (M r_k - e_k)|^2 / |r_k|^2,  A = mass^2 - D_eo D_oe,
- * i.e. the error of the network's correction measured in the residual norm, and its gradient
+ *   loss = (1/K) sum_k |A (P r_k - e_k)|^2 / |r_k|^2,  A = mass^2 - D_eo D_oe,
+ * with P = M^dag M (HISQ_PC_NORMAL) or P = M (HISQ_PC_HERMITIAN_PART), i.e. the error of the
+ * preconditioner's correction measured in the residual norm, and its gradient
  * dL/dRe W + i dL/dIm W (host or device double[HISQ_PC_WEIGHTS][2]); r, e: device FP32 internal
  * bundles of K (1..HISQ_MAX_BUNDLE) vectors each. */
 int hisq_pc_loss_grad(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,

@@ -43,6 +43,9 @@ def _bind(so):
     so.oracle_adam_step.argtypes = [ctypes.c_long, _D, _D, _D, _D, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     so.oracle_pc_backward.argtypes = [_I4, _D, _D, _D, _D, _D, _D]
+    so.oracle_pc_adjoint.argtypes = [_I4, _D, _D, _D, _D, _D]
+    so.oracle_pc_loss_grad_normal.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, _D]
+    so.oracle_pc_loss_grad_normal.restype = ctypes.c_double
     so.oracle_fcg.argtypes = [_I4, _D, _D, ctypes.c_double, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
     so.oracle_fcg.restype = ctypes.c_int
     return so
@@ -140,6 +143,28 @@ class Oracle:
         g = np.zeros_like(W)
         loss = self._so.oracle_pc_loss_grad(self._L, _p(self.X), _p(self.N), float(mass), _p(W), r.shape[0],
                                             _p(r), _p(e), _p(g) if with_grad else None)
+        return loss, g
+
+    def pc_adjoint(self, W, u):
+        """The adjoint network N^dag u on even sites (u [V/2][3])."""
+        W = _c(W).reshape(-1)
+        u = _c(u).reshape(self.V // 2, 3)
+        y = np.empty_like(u)
+        self._so.oracle_pc_adjoint(self._L, _p(self.X), _p(self.N), _p(W), _p(u), _p(y))
+        return y
+
+    def pc_normal(self, W, r):
+        """The normal form M r = N^dag N r."""
+        return self.pc_adjoint(W, self.pc_forward(W, r))
+
+    def pc_loss_grad_normal(self, W, r, e, mass: float, with_grad: bool = True):
+        """(loss, grad) of the normal form: mean_k |A (N^dag N r_k - e_k)|^2 / |r_k|^2."""
+        W = _c(W).reshape(-1)
+        r = _c(r).reshape(-1, self.V // 2, 3)
+        e = _c(e).reshape(-1, self.V // 2, 3)
+        g = np.zeros_like(W)
+        loss = self._so.oracle_pc_loss_grad_normal(self._L, _p(self.X), _p(self.N), float(mass), _p(W), r.shape[0],
+                                                   _p(r), _p(e), _p(g) if with_grad else None)
         return loss, g
 
     def pc_backward(self, W, r, gy):

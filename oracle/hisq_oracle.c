@@ -413,6 +413,93 @@ double oracle_pc_loss_grad(const int L[4], const double *X, const double *N, dou
 }
 
 /*
+ * Adjoint of one layer: g_in_{c'} = sum_path sum_c conj(W[path][c][c']) T_path^dag g_out_c, with
+ * T_path^dag the transport of the reverse hop (adjoint_path).  g_out [cout][V][3][2] ->
+ * g_in [cin][V][3][2].
+ */
+static void layer_adjoint(const int L[4], const double *X, const double *N, int cin, int cout,
+                          const double *W, const double *g_out, double *g_in) {
+    long V = volume(L), n = V * 3;
+    double *t = (double *)malloc(sizeof(double) * n * 2);
+    memset(g_in, 0, sizeof(double) * n * 2 * cin);
+    for (int path = 0; path < PC_PATHS; path++) {
+        for (int co = 0; co < cout; co++) {
+            transport(L, X, N, adjoint_path(path), g_out + (long)co * n * 2, t);
+            for (int ci = 0; ci < cin; ci++) {
+                const double *w = W + (((long)path * cout + co) * cin + ci) * 2;
+                cplx wc = c_conj((cplx){w[0], w[1]});
+                double *o = g_in + (long)ci * n * 2;
+                for (long i = 0; i < n; i++) {
+                    cplx z = c_mul(wc, (cplx){t[2 * i], t[2 * i + 1]});
+                    o[2 * i] += z.re; o[2 * i + 1] += z.im;
+                }
+            }
+        }
+    }
+    free(t);
+}
+
+/* y = M^dag u: the adjoint of the network map r -> oracle_pc_forward(r) on even sites,
+ * layer1^dag layer2^dag layer3^dag applied to u embedded on the even sites, even part kept. */
+void oracle_pc_adjoint(const int L[4], const double *X, const double *N, const double *W,
+                       const double *u, double *y) {
+    long V = volume(L), n = V * 3;
+    double *g3 = (double *)calloc((size_t)n * 2, sizeof(double));
+    double *g2 = (double *)malloc(sizeof(double) * n * 2 * 4);
+    double *g1 = (double *)malloc(sizeof(double) * n * 2 * 4);
+    double *g0 = (double *)malloc(sizeof(double) * n * 2);
+    for (long x = 0; x < V; x++)
+        if (parity_of(L, x) == 0)
+            for (int a = 0; a < 3; a++) put(g3, x, a, vec(u, x / 2, a));
+    layer_adjoint(L, X, N, 4, 1, layer_weights(W, 2), g3, g2);
+    layer_adjoint(L, X, N, 4, 4, layer_weights(W, 1), g2, g1);
+    layer_adjoint(L, X, N, 1, 4, layer_weights(W, 0), g1, g0);
+    for (long x = 0; x < V; x++)
+        if (parity_of(L, x) == 0)
+            for (int a = 0; a < 3; a++) put(y, x / 2, a, vec(g0, x, a));
+    free(g3); free(g2); free(g1); free(g0);
+}
+
+/*
+ * The same training loss for the normal form of the network, M = N^dag N (Hermitian and
+ * positive semi-definite for any weights, so preconditioned CG keeps its short recurrence):
+ *   loss = (1/K) sum_k |A (N^dag N r_k - e_k)|^2 / |r_k|^2.
+ * With h = N r, y = N^dag h and gy = 2 A A (y - e) / (K |r|^2), the weights enter twice:
+ * through N^dag (dloss = Re <h, dN gy>: the backward of N at input gy with output gradient h)
+ * and through N (dloss = Re <N gy, dN r>: the backward of N at input r with output gradient
+ * N gy).
+ */
+double oracle_pc_loss_grad_normal(const int L[4], const double *X, const double *N, double mass, const double *W,
+                                  int K, const double *r, const double *e, double *grad) {
+    long Vh = volume(L) / 2, m = Vh * 3;
+    long nw = oracle_pc_num_weights();
+    double *h = (double *)malloc(sizeof(double) * m * 2);
+    double *y = (double *)malloc(sizeof(double) * m * 2);
+    double *d = (double *)malloc(sizeof(double) * m * 2);
+    double *gy = (double *)malloc(sizeof(double) * m * 2);
+    double *ngy = (double *)malloc(sizeof(double) * m * 2);
+    double loss = 0.0;
+    if (grad) memset(grad, 0, sizeof(double) * nw * 2);
+    for (int k = 0; k < K; k++) {
+        const double *rk = r + (long)k * Vh * 6, *ek = e + (long)k * Vh * 6;
+        oracle_pc_forward(L, X, N, W, rk, h);
+        oracle_pc_adjoint(L, X, N, W, h, y);
+        for (long i = 0; i < 2 * m; i++) y[i] -= ek[i];
+        oracle_aop(L, X, N, mass, y, d, 1);                 /* d = A (y - e) */
+        double rnorm2 = norm2(rk, m);
+        loss += norm2(d, m) / rnorm2 / K;
+        if (!grad) continue;
+        oracle_aop(L, X, N, mass, d, gy, 1);                /* gy = A d */
+        for (long i = 0; i < 2 * m; i++) gy[i] *= 2.0 / (K * rnorm2);
+        oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */
+        oracle_pc_forward(L, X, N, W, gy, ngy);
+        oracle_pc_backward(L, X, N, W, rk, ngy, grad);      /* through N */
+    }
+    free(h); free(y); free(d); free(gy); free(ngy);
+    return loss;
+}
+
+/*
  * One Adam step (Kingma & Ba 2014) on n real parameters, t = step number starting at 1:
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  *   theta -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).

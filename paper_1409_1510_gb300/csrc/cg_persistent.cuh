@@ -1,13 +1,15 @@
 // The whole mixed-precision CG solve of one bundle as one cooperative, persistent kernel.
 //
-// Every phase of an iteration -- t = D_oe p, A p = m^2 p - D_eo t with <p, A p>, the update of x and
-// r with |r|^2, the decision step, the FP64 residual recomputation when one is due, and p = r + beta p
-// -- runs inside one launch, separated by grid barriers.  Each block keeps its own shared-memory copy
-// of the bundle state and evolves it identically: after a barrier every block sums the same
-// per-block partials in the same order and runs the same scalar step, so nothing has to be
-// broadcast.  The barrier is a generation counter whose wait is bounded: a block that waits longer
-// than the spin limit sets an error flag and the whole grid returns (HISQ_ERR_TIMEOUT on the host).
-// Vectors written inside the launch are read with ld.global.cg (L2), never the read-only path.
+// Every phase of an iteration -- t = D_oe p; A p = m^2 p - D_eo t with <p, A p>; the update of x
+// and r with |r|^2 and the decision step; the FP64 residual recomputation when one is due; and
+// p = r + beta p -- runs inside one launch, separated by grid barriers.  Each block owns one
+// contiguous, equal share of the sites (every SM gets the same work) and keeps its own
+// shared-memory copy of the bundle state, evolving it identically: after a barrier every block
+// sums the same per-block partials in the same order and runs the same scalar step, so nothing
+// has to be broadcast.  The barrier is a generation counter whose wait is bounded: a block that
+// waits longer than the spin limit sets an error flag and the whole grid returns
+// (HISQ_ERR_TIMEOUT on the host).  Vectors written inside the launch are read with ld.global.cg
+// (L2), never the read-only path.
 #pragma once
 #include "dslash_kernel.cuh"
 
@@ -105,13 +107,58 @@ __device__ __forceinline__ bool grid_sync(const PersArgs &a) {
     return s_ok;
 }
 
-// per-block column sums of red[rows][ndots] into partials[blockIdx.x][*]
-__device__ __forceinline__ void block_partials(const PersArgs &a, double *red, int rows, int ndots) {
+// Largest block: 1024 threads at one right-hand side per thread (64 registers), 512 otherwise
+// (128 registers); the launch may use fewer (a multiple of 32 dividing into the SM's resources).
+__host__ __device__ constexpr int pers_threads(int R) { return R == 1 ? 1024 : 512; }
+constexpr int PERS_DEFAULT_THREADS = 512;  // measured best at 32^3 x 8 (one and 16 right-hand sides)
+
+// Sites per tile for a phase whose blocks cover spb sites at a time: when the grid covers the
+// lattice in one pass, ceil(count / blocks) (every block one tile of equal size, so every SM
+// gets the same work); otherwise spb (tiles strided over the blocks).  Loops over tiles keep
+// the register footprint of the stencil within the 64 registers of a 1024-thread block.
+__device__ __forceinline__ int tile_sites(int count, int spb) {
+    return min(spb, (count + (int)gridDim.x - 1) / (int)gridDim.x);
+}
+
+// Per-block column sums of the threads' dots into partials[blockIdx.x][*].  Thread
+// tid = site_row * t + gi holds dot[r] of column gi * R + r (ndots = t * R columns).  With t a
+// power of two the lanes of one column meet in a shuffle tree and the warps' sums in one more
+// step; otherwise the dots go through red[rows][ndots] (red holds blockDim.x * R doubles).
+template <int R>
+__device__ __forceinline__ void publish_dots(const PersArgs &a, double *red, double (&dot)[R], int t, int gi,
+                                             int ndots) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    __syncthreads();  // red may still be read by the previous step
+    if ((t & (t - 1)) == 0 && t <= 32) {
+        for (int off = 16; off >= t; off >>= 1)
+#pragma unroll
+            for (int r = 0; r < R; r++) dot[r] += __shfl_xor_sync(0xffffffffu, dot[r], off);
+        if (lane < t) {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (gi * R + r < ndots) red[warp * ndots + gi * R + r] = dot[r];
+        }
+        __syncthreads();
+        for (int j = warp; j < ndots; j += nwarps) {
+            double s = lane < nwarps ? red[lane * ndots + j] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+        }
+        return;
+    }
+    const int rows = blockDim.x / t, row = tid / t;
+    for (int i = tid; i < rows * ndots; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (row < rows) {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (gi * R + r < ndots) red[row * ndots + gi * R + r] = dot[r];
+    }
     __syncthreads();
     for (int j = warp; j < ndots; j += nwarps) {
         double s = 0.0;
-        for (int row = lane; row < rows; row += 32) s += red[row * ndots + j];
+        for (int q = lane; q < rows; q += 32) s += red[q * ndots + j];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
@@ -126,7 +173,6 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
     const int per = blockDim.x / np2, j = tid % np2, k = tid / np2;
     double s = 0.0;
     if (j < ndots && k < per) {
-#pragma unroll 4
         for (int b = k; b < (int)gridDim.x; b += per) s += __ldcg(a.partials + (size_t)b * PERS_ND + j);
     }
     for (int off = 16; off >= np2; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -146,18 +192,18 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
     __syncthreads();
 }
 
-// One Dslash phase over all sites of output parity `parity`.  EPI_PLAIN: out = D in;
-// EPI_AOP: out = m^2 axpy - D in with Re<axpy, out> per block; EPI_RESID (FP64): r = b - m^2 x + D in,
-// written to out_lo (iterated precision Q) with |r|^2 per block.  mask[r] selects right-hand sides.
-template <int PP, int R, int EPI, int Q>
+// One Dslash phase over the block's share of the sites of output parity `parity`, input from the
+// loader `in`.  EPI_PLAIN: out = D in.  EPI_AOP: out = m^2 ax - D in with Re<ax, out> per block
+// (ax from the loader `ax` at the output site).  EPI_RESID (FP64): r = b - m^2 ax + D in, written
+// to out_lo (iterated precision Q) with |r|^2 per block.  mask[r] selects right-hand sides.
+template <int PP, int R, int EPI, int Q, class IN, class AX>
 __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
-                                             const void *in, void *out, int parity, const int *mask,
-                                             const void *axpy, const void *bvec, void *out_lo, double *red) {
+                                             const IN &in, void *out, int parity, const int *mask, const AX &ax,
+                                             const void *bvec, void *out_lo, double *red) {
     using real = typename Prec<PP>::real;
     const Geom &g = a.g;
     const int n = a.n, t = n / R, spb = blockDim.x / t;
     const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = gi * R;
-    const VecView<PP> vin{const_cast<void *>(in), n};
     const VecView<PP> vout{out, n};
     bool act[R];
     bool any = false;
@@ -169,79 +215,70 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
     double dot[R];
 #pragma unroll
     for (int r = 0; r < R; r++) dot[r] = 0.0;
-    for (int tile = blockIdx.x; (long)tile * spb < g.Vh; tile += gridDim.x) {
-        const int s = tile * spb + sl;
-        if (sl >= spb || s >= g.Vh || !any) continue;
-        Cplx<real> acc[R][3];
+    const int ts = tile_sites(g.Vh, spb);
+    if (any && sl < ts) {
+        for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
+            const int s = tile * ts + sl;
+            if (s >= g.Vh) break;
+            Cplx<real> acc[R][3];
+            site_stencil<PP, 18, R, 1>(g, fat, naik, parity, in, s, 0, r0, act, acc);
+            if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
-        for (int r = 0; r < R; r++)
+                for (int r = 0; r < R; r++)
+                    if (act[r]) store_vec<PP>(vout, s, r0 + r, acc[r]);
+            } else if constexpr (EPI == EPI_AOP) {
+                const real m2 = (real)a.mass2;
+                Cplx<real> p[R][3];
+                ax.template load<R>(s, r0, act, p);
 #pragma unroll
-            for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
-        site_stencil<PP, 18, R, 1, true>(g, fat, naik, parity, vin, s, 0, r0, act, acc);
-        if constexpr (EPI == EPI_PLAIN) {
+                for (int r = 0; r < R; r++) {
+                    if (!act[r]) continue;
+                    Cplx<real> w[3];
+                    real d = 0;
 #pragma unroll
-            for (int r = 0; r < R; r++)
-                if (act[r]) store_vec<PP>(vout, s, r0 + r, acc[r]);
-        } else if constexpr (EPI == EPI_AOP) {
-            const VecView<PP> vp{const_cast<void *>(axpy), n};
-            const real m2 = (real)a.mass2;
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                if (!act[r]) continue;
-                Cplx<real> p[3], w[3];
-                load_vec<PP, true>(vp, s, r0 + r, p);
-                real d = 0;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    w[c] = {m2 * p[c].re - acc[r][c].re, m2 * p[c].im - acc[r][c].im};
-                    d += p[c].re * w[c].re + p[c].im * w[c].im;
+                    for (int c = 0; c < 3; c++) {
+                        w[c] = {m2 * p[r][c].re - acc[r][c].re, m2 * p[r][c].im - acc[r][c].im};
+                        d += p[r][c].re * w[c].re + p[r][c].im * w[c].im;
+                    }
+                    dot[r] += (double)d;
+                    store_vec<PP>(vout, s, r0 + r, w);
                 }
-                dot[r] += (double)d;
-                store_vec<PP>(vout, s, r0 + r, w);
-            }
-        } else {
-            static_assert(EPI == EPI_RESID && PP == HISQ_FP64, "residual epilogue is FP64");
-            const VecView<HISQ_FP64> vx{const_cast<void *>(axpy), n}, vb{const_cast<void *>(bvec), n};
-            const VecView<Q> vlo{out_lo, n};
+            } else {
+                static_assert(EPI == EPI_RESID && PP == HISQ_FP64, "residual epilogue is FP64");
+                const VecView<HISQ_FP64> vb{const_cast<void *>(bvec), n};
+                const VecView<Q> vlo{out_lo, n};
+                Cplx<double> x[R][3];
+                ax.template load<R>(s, r0, act, x);
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                if (!act[r]) continue;
-                Cplx<double> x[3], b[3];
-                Cplx<typename Prec<Q>::real> lo[3];
-                load_vec<HISQ_FP64, true>(vx, s, r0 + r, x);
-                load_vec<HISQ_FP64, true>(vb, s, r0 + r, b);
-                double d = 0.0;
+                for (int r = 0; r < R; r++) {
+                    if (!act[r]) continue;
+                    Cplx<double> b[3];
+                    Cplx<typename Prec<Q>::real> lo3[3];
+                    load_vec<HISQ_FP64, true>(vb, s, r0 + r, b);
+                    double d = 0.0;
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    double wr = b[c].re - a.mass2 * x[c].re + (double)acc[r][c].re;
-                    double wi = b[c].im - a.mass2 * x[c].im + (double)acc[r][c].im;
-                    d += wr * wr + wi * wi;
-                    lo[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+                    for (int c = 0; c < 3; c++) {
+                        double wr = b[c].re - a.mass2 * x[r][c].re + (double)acc[r][c].re;
+                        double wi = b[c].im - a.mass2 * x[r][c].im + (double)acc[r][c].im;
+                        d += wr * wr + wi * wi;
+                        lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+                    }
+                    dot[r] += d;
+                    store_vec<Q>(vlo, s, r0 + r, lo3);
                 }
-                dot[r] += d;
-                store_vec<Q>(vlo, s, r0 + r, lo);
             }
         }
     }
-    if constexpr (EPI != EPI_PLAIN) {
-        for (int i = tid; i < spb * n; i += blockDim.x) red[i] = 0.0;
-        __syncthreads();
-        if (sl < spb) {
-#pragma unroll
-            for (int r = 0; r < R; r++)
-                if (r0 + r < n) red[sl * n + r0 + r] = dot[r];
-        }
-        block_partials(a, red, spb, n);
-    }
+    if constexpr (EPI != EPI_PLAIN) publish_dots<R>(a, red, dot, t, gi, n);
 }
 
 // the solve loop (body in cg_persistent_body.cuh, instantiated per precision)
 template <int P, int R>
-__global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(PersArgs a);
+__global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const __grid_constant__ PersArgs a);
 
 template <int P>
-cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t st);
 template <int P>
-cudaError_t persistent_occupancy(int R, size_t smem, int *blocks_per_sm);
+cudaError_t persistent_occupancy(int R, int threads, size_t smem, int *blocks_per_sm);
 
 }  // namespace hisq

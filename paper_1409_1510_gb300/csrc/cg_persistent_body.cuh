@@ -4,18 +4,16 @@
 
 namespace hisq {
 
-// With one right-hand side per thread, four 256-thread blocks per SM (at most 64 registers) keep
-// every site of a 32^3 x 8 parity resident in a single pass of each Dslash phase.
 template <int P, int R>
-__global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(PersArgs a) {
+__global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const __grid_constant__ PersArgs a) {
     constexpr int Q = q_prec(P);
     using rp = typename Prec<P>::real;
     using rq = typename Prec<Q>::real;
     extern __shared__ double red[];
     __shared__ SolverState st;
     __shared__ double dots[PERS_ND];
+    __shared__ PhaseClock clk;
     const int tid = threadIdx.x, n = a.n;
-    const long Vh = a.g.Vh;
     {
         constexpr int WORDS = sizeof(SolverState) / sizeof(uint32_t);
         const uint32_t *src = reinterpret_cast<const uint32_t *>(a.st);
@@ -23,41 +21,42 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         for (int i = tid; i < WORDS; i += blockDim.x) dst[i] = __ldcg(src + i);
     }
     __syncthreads();
-    // BLAS phases: thread (site row sl, right-hand side r)
+    // vector phases: thread (site row sl, right-hand side r) over the block's share of the sites
     const int r = tid % n, spb = blockDim.x / n, sl = tid / n;
-    const VecView<HISQ_FP64> vb{a.b, n}, vxh{a.xhi, n};
-    const VecView<Q> vx{a.x, n}, vr{a.r, n};
-    const VecView<P> vp{a.p, n}, vap{a.ap, n};
-    auto publish = [&](double acc) {
-        for (int i = tid; i < spb * n; i += blockDim.x) red[i] = 0.0;
-        __syncthreads();
-        if (sl < spb) red[sl * n + r] = acc;
-        block_partials(a, red, spb, n);
-    };
+    const int ts = tile_sites(a.g.Vh, spb);
+    // views are rebuilt from the (constant-bank) arguments where they are used: nothing of them
+    // stays live in registers across the Dslash phases
+#define V64(f) VecView<HISQ_FP64>{a.f, n}
+#define VQ(f) VecView<Q>{a.f, n}
+#define VP(f) VecView<P>{a.f, n}
+    const bool row_ok = sl < ts;
 
     // ---- setup: x_hi = 0, x = 0, r = b, p = b and |b|^2 ----
     {
-        double acc = 0.0;
-        for (long tile = blockIdx.x; tile * spb < Vh; tile += gridDim.x) {
-            const long s = tile * spb + sl;
-            if (sl >= spb || s >= Vh) continue;
-            Cplx<double> b[3];
-            load_vec<HISQ_FP64, true>(vb, s, r, b);
-            Cplx<double> z64[3] = {{0, 0}, {0, 0}, {0, 0}};
-            Cplx<rq> zq[3] = {{0, 0}, {0, 0}, {0, 0}}, bq[3];
-            Cplx<rp> bp[3];
+        double acc[1] = {0.0};
+        if (row_ok) {
+            for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
+                const int s = tile * ts + sl;
+                if (s >= a.g.Vh) break;
+                Cplx<double> b[3];
+                load_vec<HISQ_FP64, true>(V64(b), s, r, b);
+                const Cplx<double> z64[3] = {{0, 0}, {0, 0}, {0, 0}};
+                const Cplx<rq> zq[3] = {{0, 0}, {0, 0}, {0, 0}};
+                Cplx<rq> bq[3];
+                Cplx<rp> bp[3];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                acc += b[c].re * b[c].re + b[c].im * b[c].im;
-                bq[c] = {(rq)b[c].re, (rq)b[c].im};
-                bp[c] = {(rp)b[c].re, (rp)b[c].im};
+                for (int c = 0; c < 3; c++) {
+                    acc[0] += b[c].re * b[c].re + b[c].im * b[c].im;
+                    bq[c] = {(rq)b[c].re, (rq)b[c].im};
+                    bp[c] = {(rp)b[c].re, (rp)b[c].im};
+                }
+                store_vec<HISQ_FP64>(V64(xhi), s, r, z64);
+                store_vec<Q>(VQ(x), s, r, zq);
+                store_vec<Q>(VQ(r), s, r, bq);
+                store_vec<P>(VP(p), s, r, bp);
             }
-            store_vec<HISQ_FP64>(vxh, s, r, z64);
-            store_vec<Q>(vx, s, r, zq);
-            store_vec<Q>(vr, s, r, bq);
-            store_vec<P>(vp, s, r, bp);
         }
-        publish(acc);
+        publish_dots<1>(a, red, acc, n, r, n);
     }
     bool ok = grid_sync(a);
     if (ok) {
@@ -65,16 +64,17 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         if (tid == 0) run_hook(HOOK_INIT, &st, dots, n);
         __syncthreads();
     }
-    __shared__ PhaseClock clk;
     clock_start(clk, a.phase_ns);
 
     while (ok && st.any_active && st.bundle_iters < st.max_iter) {
         // t = D_oe p
-        dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, a.p, a.t, 1, st.active, nullptr, nullptr, nullptr, red);
+        dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(p)}, a.t, 1, st.active,
+                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_DOE);
         // A p = m^2 p - D_eo t and <p, A p>
-        dslash_phase<P, R, EPI_AOP, Q>(a, a.fat, a.naik, a.t, a.ap, 0, st.active, a.p, nullptr, nullptr, red);
+        dslash_phase<P, R, EPI_AOP, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active,
+                                       PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
         if (!(ok = grid_sync(a))) break;
         sum_partials(a, red, n, dots);
         if (tid == 0) run_hook(HOOK_ALPHA, &st, dots, n);
@@ -82,18 +82,18 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         clock_mark(clk, PH_AOP);
         // x += alpha p; r -= alpha A p; |r|^2
         {
-            double acc = 0.0;
-            if (st.active[r]) {
+            double acc[1] = {0.0};
+            if (st.active[r] && row_ok) {
                 const rq al = (rq)st.alpha[r][0];
-                for (long tile = blockIdx.x; tile * spb < Vh; tile += gridDim.x) {
-                    const long s = tile * spb + sl;
-                    if (sl >= spb || s >= Vh) continue;
+                for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
+                    const int s = tile * ts + sl;
+                    if (s >= a.g.Vh) break;
                     Cplx<rp> p[3], ap[3];
                     Cplx<rq> x[3], rv[3];
-                    load_vec<P, true>(vp, s, r, p);
-                    load_vec<P, true>(vap, s, r, ap);
-                    load_vec<Q, true>(vx, s, r, x);
-                    load_vec<Q, true>(vr, s, r, rv);
+                    load_vec<P, true>(VP(p), s, r, p);
+                    load_vec<P, true>(VP(ap), s, r, ap);
+                    load_vec<Q, true>(VQ(x), s, r, x);
+                    load_vec<Q, true>(VQ(r), s, r, rv);
                     rq part = 0;
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
@@ -103,12 +103,12 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
                         rv[c].im -= al * (rq)ap[c].im;
                         part += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
                     }
-                    acc += (double)part;
-                    store_vec<Q>(vx, s, r, x);
-                    store_vec<Q>(vr, s, r, rv);
+                    acc[0] += (double)part;
+                    store_vec<Q>(VQ(x), s, r, x);
+                    store_vec<Q>(VQ(r), s, r, rv);
                 }
             }
-            publish(acc);
+            publish_dots<1>(a, red, acc, n, r, n);
         }
         if (!(ok = grid_sync(a))) break;
         sum_partials(a, red, n, dots);
@@ -117,26 +117,28 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
         clock_mark(clk, PH_UPDATE);
         if (st.any_update) {
             // reliable update: x_hi += x; x = 0; r = b - A x_hi in FP64 (written to r), |r|^2
-            if (st.update[r]) {
-                for (long tile = blockIdx.x; tile * spb < Vh; tile += gridDim.x) {
-                    const long s = tile * spb + sl;
-                    if (sl >= spb || s >= Vh) continue;
-                    Cplx<rq> x[3], zq[3] = {{0, 0}, {0, 0}, {0, 0}};
+            if (st.update[r] && row_ok) {
+                for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
+                    const int s = tile * ts + sl;
+                    if (s >= a.g.Vh) break;
+                    Cplx<rq> x[3];
+                    const Cplx<rq> zq[3] = {{0, 0}, {0, 0}, {0, 0}};
                     Cplx<double> xh[3];
-                    load_vec<Q, true>(vx, s, r, x);
-                    load_vec<HISQ_FP64, true>(vxh, s, r, xh);
+                    load_vec<Q, true>(VQ(x), s, r, x);
+                    load_vec<HISQ_FP64, true>(V64(xhi), s, r, xh);
 #pragma unroll
                     for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
-                    store_vec<HISQ_FP64>(vxh, s, r, xh);
-                    store_vec<Q>(vx, s, r, zq);
+                    store_vec<HISQ_FP64>(V64(xhi), s, r, xh);
+                    store_vec<Q>(VQ(x), s, r, zq);
                 }
             }
             if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, a.xhi, a.t64, 1, st.update, nullptr, nullptr,
-                                                     nullptr, red);
+            dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
+                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr,
+                                                     red);
             if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, a.t64, nullptr, 0, st.update, a.xhi, a.b,
-                                                     a.r, red);
+            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
+                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red);
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, n, dots);
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
@@ -144,23 +146,26 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
             clock_mark(clk, PH_RELIABLE);
         }
         // p = r + beta p
-        if (st.active[r]) {
+        if (st.active[r] && row_ok) {
             const rp be = (rp)st.beta[r][0];
-            for (long tile = blockIdx.x; tile * spb < Vh; tile += gridDim.x) {
-                const long s = tile * spb + sl;
-                if (sl >= spb || s >= Vh) continue;
+            for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
+                const int s = tile * ts + sl;
+                if (s >= a.g.Vh) break;
                 Cplx<rq> rv[3];
                 Cplx<rp> p[3];
-                load_vec<Q, true>(vr, s, r, rv);
-                load_vec<P, true>(vp, s, r, p);
+                load_vec<Q, true>(VQ(r), s, r, rv);
+                load_vec<P, true>(VP(p), s, r, p);
 #pragma unroll
                 for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
-                store_vec<P>(vp, s, r, p);
+                store_vec<P>(VP(p), s, r, p);
             }
         }
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_PUPDATE);
     }
+#undef V64
+#undef VQ
+#undef VP
     clock_store(clk, a.phase_ns);
     if (blockIdx.x == 0) {  // the final bundle state for the host
         __syncthreads();
@@ -171,21 +176,27 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : 2) cg_persistent_kernel(Pers
     }
 }
 
+// the instantiation for R right-hand sides per thread (FP64 stops at two: four would spill)
 template <int P>
-cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, size_t smem, cudaStream_t st) {
-    void *args[] = {const_cast<PersArgs *>(&a)};
-    const void *k = R == 4 ? (const void *)cg_persistent_kernel<P, 4>
-                  : R == 2 ? (const void *)cg_persistent_kernel<P, 2>
-                           : (const void *)cg_persistent_kernel<P, 1>;
-    return cudaLaunchCooperativeKernel(k, grid, 256, args, smem, st);
+const void *persistent_kernel_ptr(int R) {
+    if constexpr (P != HISQ_FP64) {
+        if (R == 4) return (const void *)cg_persistent_kernel<P, 4>;
+    }
+    if (R >= 2) return (const void *)cg_persistent_kernel<P, 2>;
+    return (const void *)cg_persistent_kernel<P, 1>;
 }
 
 template <int P>
-cudaError_t persistent_occupancy(int R, size_t smem, int *blocks_per_sm) {
-    const void *k = R == 4 ? (const void *)cg_persistent_kernel<P, 4>
-                  : R == 2 ? (const void *)cg_persistent_kernel<P, 2>
-                           : (const void *)cg_persistent_kernel<P, 1>;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 256, smem);
+cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t st) {
+    void *args[] = {const_cast<PersArgs *>(&a)};
+    if (P == HISQ_FP64 && R > 2) return cudaErrorInvalidValue;
+    return cudaLaunchCooperativeKernel(persistent_kernel_ptr<P>(R), grid, threads, args, smem, st);
+}
+
+template <int P>
+cudaError_t persistent_occupancy(int R, int threads, size_t smem, int *blocks_per_sm) {
+    if (P == HISQ_FP64 && R > 2) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel_ptr<P>(R), threads, smem);
 }
 
 }  // namespace hisq

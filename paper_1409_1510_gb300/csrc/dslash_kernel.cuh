@@ -178,6 +178,18 @@ __device__ __forceinline__ void load_neighbours(const VecView<P> &vin, int nb, i
     }
 }
 
+// Input of the stencil: the colour vectors of one bundle as stored (COHERENT: read through L2,
+// for vectors written earlier in the same launch).  Other inputs (a direction formed on the fly)
+// provide the same load().
+template <int P, bool COHERENT>
+struct PlainIn {
+    VecView<P> v;
+    template <int R>
+    __device__ __forceinline__ void load(int nb, int r0, const bool act[R], Cplx<typename Prec<P>::real> out[R][3]) const {
+        load_neighbours<P, R, COHERENT>(v, nb, r0, act, out);
+    }
+};
+
 // acc *= f
 template <typename T, int R>
 __device__ __forceinline__ void scale_acc(Cplx<T> acc[R][3], T f) {
@@ -188,17 +200,17 @@ __device__ __forceinline__ void scale_acc(Cplx<T> acc[R][3], T f) {
 }
 
 // The stencil of Eq. (3) at output site s (parity `parity`): writes into acc the sum of the
-// products of the site's links with the neighbouring input vectors of the R right-hand sides
-// r0.. that are active.  S = 1: all 16 links.  S = 2 (18-real Naik only): the 8 fat (part 0) or
-// the 8 Naik links (part 1).  S = 4 (18-real Naik only): part = 2 kind + half, the four links of
-// directions 2 half and 2 half + 1 of that kind.  Record slot 2 mu holds the forward link of
+// products of the site's links with the neighbouring input vectors (from the loader `vin`) of
+// the R right-hand sides r0.. that are active.  S = 1: all 16 links.  S = 2 (18-real Naik only):
+// the 8 fat (part 0) or the 8 Naik links (part 1).  S = 4 (18-real Naik only): part =
+// 2 kind + half, the four links of directions 2 half and 2 half + 1 of that kind.  Record slot 2 mu holds the forward link of
 // direction mu and slot 2 mu + 1 the backward one (already -U^dagger of the neighbour's link).
 // 16-bit 18-real records carry one positive float scale per (parity, site) and field; it is
 // applied to the field's summed contribution (6 R products) instead of to the 18 reals of each
 // of its links: with both fields scaled, acc = s_N (s_X / s_N sum_X + sum_N).
-template <int P, int NR, int R, int S, bool COHERENT>
+template <int P, int NR, int R, int S, class IN>
 __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat_f, const LinkField &naik_f, int parity,
-                                             const VecView<P> &vin, int s, int part, int r0, const bool act[R],
+                                             const IN &vin, int s, int part, int r0, const bool act[R],
                                              Cplx<typename Prec<P>::real> acc[R][3]) {
     using real = typename Prec<P>::real;
     using FatC = LinkCodec<P, 18>;
@@ -228,7 +240,7 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
                 Cplx<real> M[3][3];
                 FatC::decode(u, l, M);
                 Cplx<real> v[R][3];
-                load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
+                vin.template load<R>(nb, r0, act, v);
                 matvec_acc<real, R>(M, v, acc);
             }
         }
@@ -254,7 +266,7 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
                     Cplx<real> M[3][3];
                     NaikC::decode(u, l, M);
                     Cplx<real> v[R][3];
-                    load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
+                    vin.template load<R>(nb, r0, act, v);
                     matvec_acc<real, R>(M, v, acc);
                 }
             }
@@ -275,7 +287,7 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
                 Cplx<real> M[3][3];
                 FatC::decode(u, l, M);
                 Cplx<real> v[R][3];
-                load_neighbours<P, R, COHERENT>(vin, nb, r0, act, v);
+                vin.template load<R>(nb, r0, act, v);
                 matvec_acc<real, R>(M, v, acc);
             }
         }
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
     const int sl = tid / (S * a.t);
     const int r0 = gi * R;
     const int nvalid = min(R, a.n - r0);
-    const VecView<P> vin = view<P>(a.in, g.Vh, a.n);
+    const PlainIn<P, false> vin{view<P>(a.in, g.Vh, a.n)};
     const VecView<P> vout = view<P>(a.out, g.Vh, a.n);
 
     bool act[R];
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
 
-        if (valid) site_stencil<P, NR, R, S, false>(g, a.fat, a.naik, a.parity, vin, s, part, r0, act, acc);
+        if (valid) site_stencil<P, NR, R, S>(g, a.fat, a.naik, a.parity, vin, s, part, r0, act, acc);
         if constexpr (S > 1) {
             // add the lanes' parts; every lane of the warp takes part
 #pragma unroll

@@ -224,6 +224,7 @@ struct hisq_pc {
     float2 *d_weights;                     // device FP32 copy used by the kernels
     double *d_theta, *d_m, *d_v;           // Adam state on the device (FP64, real parameters)
     void *work;                            // network workspace (pc.cu)
+    int form;                              // HISQ_PC_NORMAL or HISQ_PC_HERMITIAN_PART
 };
 
 namespace hisq {
@@ -255,6 +256,7 @@ struct hisq_ctx {
     int num_sms;
     hisq_solver_params params;
     std::map<hisq::TuneKey, hisq::LaunchShape> tuned;
+    std::map<hisq::TuneKey, float> tuned_ms;  // median time of the chosen shape (L2 flushed)
     unsigned tune_generation = 0;  // bumped whenever a launch shape changes (captured graphs go stale)
     // generic scratch: reductions (partials + counter) and the A-operator intermediate
     double *partials;       // [max_blocks * HISQ_MAX_NRHS * 2]
@@ -314,12 +316,13 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
                   const DslashArgs &a, const LaunchShape *shape, cudaStream_t stream, int *grid_out = nullptr);
 LaunchShape default_shape(int prec, int n);
 LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64);
+int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64);  // tune.cu
 void free_workspace(hisq_ctx *ctx);  // solver.cu
 void free_pc(hisq_pc *pc);           // pc.cu
 int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
                void *out, int n, cudaStream_t st);
-int pc_forward_hermitian(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
-                         const void *in, void *out, int n, cudaStream_t st);
+int pc_forward_precond(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                       const void *in, void *out, int n, cudaStream_t st);  // the handle's form
 int pc_prepare(hisq_ctx *ctx, const hisq_pc *pc, int n);  // allocate the network workspace
 int pack_vectors(hisq_ctx *ctx, const double *canon_dev, void *internal, int n, int prec, cudaStream_t st);
 int unpack_vectors(hisq_ctx *ctx, const void *internal, double *canon_dev, int n, int prec, cudaStream_t st);

@@ -97,8 +97,10 @@ struct PcWork {
     float2 *y = nullptr, *G3 = nullptr;   // 1 channel, even
     float2 *u = nullptr, *d = nullptr;    // 1 channel, even: y - e and A (y - e)
     float2 *t = nullptr;                  // 1 channel, odd: intermediate of A
+    float2 *hN = nullptr, *gy = nullptr;  // 1 channel, even: M r and the output gradient (normal form)
     double *r2 = nullptr, *dots = nullptr;
     double *gbuf = nullptr;               // [3 layers][2 parity][17*16*2]
+    double *gbuf2 = nullptr;              // first of the two gradient terms of the normal form
     double *e2 = nullptr, *err2 = nullptr, *grad = nullptr;
     double *partials = nullptr;
     size_t partials_cap = 0;
@@ -119,7 +121,8 @@ static void free_work(PcWork &w) {
         if (w.g2[p]) cudaFree(w.g2[p]);
         w.h1[p] = w.h2[p] = w.g1[p] = w.g2[p] = nullptr;
     }
-    void *bufs[] = {w.y, w.G3, w.u, w.d, w.t, w.r2, w.dots, w.gbuf, w.e2, w.err2, w.grad, w.partials, w.counter};
+    void *bufs[] = {w.y, w.G3, w.u, w.d, w.t, w.hN, w.gy, w.r2, w.dots, w.gbuf, w.gbuf2, w.e2, w.err2, w.grad,
+                    w.partials, w.counter};
     for (void *b : bufs)
         if (b) cudaFree(b);
     w = PcWork();
@@ -138,9 +141,11 @@ static int ensure_work(hisq_ctx *ctx, hisq_pc *pc, int K) {
              cudaMalloc(&w.g1[p], f4) == cudaSuccess && cudaMalloc(&w.g2[p], f4) == cudaSuccess;
     ok = ok && cudaMalloc(&w.y, f1) == cudaSuccess && cudaMalloc(&w.G3, f1) == cudaSuccess &&
          cudaMalloc(&w.u, f1) == cudaSuccess && cudaMalloc(&w.d, f1) == cudaSuccess &&
-         cudaMalloc(&w.t, f1) == cudaSuccess && cudaMalloc(&w.r2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
+         cudaMalloc(&w.t, f1) == cudaSuccess && cudaMalloc(&w.hN, f1) == cudaSuccess &&
+         cudaMalloc(&w.gy, f1) == cudaSuccess && cudaMalloc(&w.r2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
          cudaMalloc(&w.dots, sizeof(double) * HISQ_MAX_BUNDLE * 4) == cudaSuccess &&
          cudaMalloc(&w.gbuf, sizeof(double) * 3 * 2 * PC_PATHS * 16 * 2) == cudaSuccess &&
+         cudaMalloc(&w.gbuf2, sizeof(double) * 3 * 2 * PC_PATHS * 16 * 2) == cudaSuccess &&
          cudaMalloc(&w.e2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
          cudaMalloc(&w.err2, sizeof(double) * HISQ_MAX_BUNDLE) == cudaSuccess &&
          cudaMalloc(&w.grad, sizeof(double) * 2 * HISQ_PC_WEIGHTS) == cudaSuccess &&
@@ -304,6 +309,26 @@ static int forward_hermitian(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, 
     return HISQ_OK;
 }
 
+// out = M^dag M in, the normal form of the network
+static int forward_normal(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const float2 *in,
+                          float2 *out, int K, cudaStream_t st) {
+    PcWork &w = pcw(pc);
+    HISQ_CHECK(forward(ctx, pc, fat, naik, in, w.y, K, st));
+    return forward_adjoint(ctx, pc, fat, naik, w.y, out, K, st);
+}
+
+// the preconditioner of the handle's form
+static int forward_precond(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                           const float2 *in, float2 *out, int K, cudaStream_t st) {
+    if (pc->form == HISQ_PC_NORMAL) return forward_normal(ctx, pc, fat, naik, in, out, K, st);
+    return forward_hermitian(ctx, pc, fat, naik, in, out, K, st);
+}
+
+__global__ void pc_add_kernel(int n, double *a, const double *b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += b[i];
+}
+
 static RedArgs red_of(PcWork &w, double *dot_out) {
     RedArgs r;
     r.partials = w.partials;
@@ -434,6 +459,55 @@ static int loss_and_grad(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, cons
     return backward(ctx, pc, fat, naik, r, K, st);
 }
 
+// The normal form P = M^dag M: loss = mean_k |A (P r_k - e_k)|^2 / |r_k|^2.  With h = M r,
+// y = M^dag h and gy = 2 A A (y - e) / (K |r|^2) the weights enter twice: through M^dag (the
+// backward of M at input gy with output gradient h) and through M (the backward of M at input r
+// with output gradient M gy); the two weight gradients are added.
+static int loss_and_grad_normal(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
+                                const float2 *r, const float2 *e, int K, cudaStream_t st) {
+    PcWork &w = pcw(pc);
+    const long n = (long)ctx->geom.Vh * 3 * K;
+    const size_t fbytes = sizeof(float2) * n;
+    const int blocks = (int)std::min<long>((n + 255) / 256, (long)ctx->num_sms * 8);
+    const int ng = 3 * 2 * PC_PATHS * 16 * 2;
+    LossArgs a;
+    memset(&a, 0, sizeof(a));
+    a.Vh = ctx->geom.Vh;
+    a.K = K;
+    a.spb = pow2_floor_pc(256 / K);
+    a.e = r;
+    a.red = red_of(w, w.r2);
+    HISQ_CHECK(reduce_launch(ctx, pc_norm_kernel, a, st));                 // |r_k|^2
+    HISQ_CHECK(forward(ctx, pc, fat, naik, r, w.hN, K, st));                // h = M r
+    HISQ_CHECK(forward_adjoint(ctx, pc, fat, naik, w.hN, w.u, K, st));     // y = M^dag h
+    pc_sub_kernel<<<blocks, 256, 0, st>>>(n, w.u, e, w.u);                  // u = y - e
+    HISQ_CHECK(apply_a(ctx, fat, naik, w, mass, w.u, w.d, K, st));          // d = A u
+    a.e = w.d;
+    a.red = red_of(w, w.err2);
+    HISQ_CHECK(reduce_launch(ctx, pc_norm_kernel, a, st));                 // |d_k|^2
+    HISQ_CHECK(apply_a(ctx, fat, naik, w, mass, w.d, w.gy, K, st));         // gy = A d
+    pc_scale_kernel<<<blocks, 256, 0, st>>>(n, K, w.r2, w.gy);              // gy *= 2 / (K |r|^2)
+    HISQ_CUDA(cudaGetLastError());
+    // through M^dag: forward at input gy (its activations; output M gy kept in y), gradient h
+    HISQ_CHECK(forward(ctx, pc, fat, naik, w.gy, w.y, K, st));
+    HISQ_CUDA(cudaMemcpyAsync(w.G3, w.hN, fbytes, cudaMemcpyDeviceToDevice, st));
+    HISQ_CHECK(backward(ctx, pc, fat, naik, w.gy, K, st));
+    HISQ_CUDA(cudaMemcpyAsync(w.gbuf2, w.gbuf, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st));
+    // through M: forward at input r again (its activations), gradient M gy
+    HISQ_CHECK(forward(ctx, pc, fat, naik, r, w.u, K, st));
+    HISQ_CUDA(cudaMemcpyAsync(w.G3, w.y, fbytes, cudaMemcpyDeviceToDevice, st));
+    HISQ_CHECK(backward(ctx, pc, fat, naik, r, K, st));
+    pc_add_kernel<<<(ng + 255) / 256, 256, 0, st>>>(ng, w.gbuf, w.gbuf2);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
+}
+
+static int loss_and_grad_form(hisq_ctx *ctx, hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
+                              const float2 *r, const float2 *e, int K, cudaStream_t st) {
+    if (pc->form == HISQ_PC_NORMAL) return loss_and_grad_normal(ctx, pc, fat, naik, mass, r, e, K, st);
+    return loss_and_grad(ctx, pc, fat, naik, mass, r, e, K, st);
+}
+
 static int check_args(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik) {
     if (!pc || !fat || !naik) return set_error(HISQ_ERR_ARG, "null argument");
     if (pc->ctx != ctx || fat->ctx != ctx || naik->ctx != ctx) return set_error(HISQ_ERR_STATE, "handle of another context");
@@ -474,12 +548,12 @@ int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hi
     return forward(ctx, m, fat, naik, reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out), n, st);
 }
 
-int pc_forward_hermitian(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
-                         const void *in, void *out, int n, cudaStream_t st) {
+int pc_forward_precond(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik,
+                       const void *in, void *out, int n, cudaStream_t st) {
     hisq_pc *m = const_cast<hisq_pc *>(pc);
     HISQ_CHECK(ensure_work(ctx, m, n));
-    return forward_hermitian(ctx, m, fat, naik, reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out),
-                             n, st);
+    return forward_precond(ctx, m, fat, naik, reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out), n,
+                           st);
 }
 
 }  // namespace hisq
@@ -500,6 +574,7 @@ int hisq_pc_create(hisq_pc **out, const double *weights) {
         for (int l = 0; l < 3; l++) pc->weights[2 * pc_layer_offset(l)] = 1.0;
     }
     pc->ctx = ctx;
+    pc->form = HISQ_PC_NORMAL;
     pc->work = new PcState();
     bool ok = cudaMalloc(&pc->d_weights, sizeof(float2) * HISQ_PC_WEIGHTS) == cudaSuccess &&
               cudaMalloc(&pc->d_theta, sizeof(pc->weights)) == cudaSuccess &&
@@ -564,14 +639,48 @@ int hisq_pc_apply(const hisq_pc *pc, const hisq_links *fat, const hisq_links *na
     return pc_forward(ctx, pc, fat, naik, in, out, nrhs, ctx->stream);
 }
 
-int hisq_pc_apply_hermitian(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
-                            void *out, int nrhs) {
+// the three operators of the network beyond M itself
+enum { APPLY_ADJOINT, APPLY_HERMITIAN, APPLY_NORMAL };
+
+static int apply_op(int op, const hisq_pc *pc_c, const hisq_links *fat, const hisq_links *naik, const void *in,
+                    void *out, int nrhs) {
     hisq_ctx *ctx;
     HISQ_CHECK(require_ctx(&ctx));
-    HISQ_CHECK(check_args(ctx, pc, fat, naik));
+    HISQ_CHECK(check_args(ctx, pc_c, fat, naik));
     if (!in || !out || in == out) return set_error(HISQ_ERR_ARG, "bad vectors");
     if (nrhs < 1 || nrhs > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "nrhs must be in 1..%d", HISQ_MAX_BUNDLE);
-    return pc_forward_hermitian(ctx, pc, fat, naik, in, out, nrhs, ctx->stream);
+    hisq_pc *pc = const_cast<hisq_pc *>(pc_c);
+    HISQ_CHECK(ensure_work(ctx, pc, nrhs));
+    const float2 *x = reinterpret_cast<const float2 *>(in);
+    float2 *y = reinterpret_cast<float2 *>(out);
+    if (op == APPLY_ADJOINT) return forward_adjoint(ctx, pc, fat, naik, x, y, nrhs, ctx->stream);
+    if (op == APPLY_HERMITIAN) return forward_hermitian(ctx, pc, fat, naik, x, y, nrhs, ctx->stream);
+    return forward_normal(ctx, pc, fat, naik, x, y, nrhs, ctx->stream);
+}
+
+int hisq_pc_apply_adjoint(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in, void *out,
+                          int nrhs) {
+    return apply_op(APPLY_ADJOINT, pc, fat, naik, in, out, nrhs);
+}
+
+int hisq_pc_apply_hermitian(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
+                            void *out, int nrhs) {
+    return apply_op(APPLY_HERMITIAN, pc, fat, naik, in, out, nrhs);
+}
+
+int hisq_pc_apply_normal(const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in, void *out,
+                         int nrhs) {
+    return apply_op(APPLY_NORMAL, pc, fat, naik, in, out, nrhs);
+}
+
+int hisq_pc_set_form(hisq_pc *pc, int form) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!pc) return set_error(HISQ_ERR_ARG, "null handle");
+    if (pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "handle of another context");
+    if (form != HISQ_PC_NORMAL && form != HISQ_PC_HERMITIAN_PART) return set_error(HISQ_ERR_ARG, "unknown form %d", form);
+    pc->form = form;
+    return HISQ_OK;
 }
 
 int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_links *naik, double mass, const void *r,
@@ -585,8 +694,8 @@ int hisq_pc_loss_grad(const hisq_pc *pc_c, const hisq_links *fat, const hisq_lin
     HISQ_CHECK(ensure_work(ctx, pc, K));
     PcWork &w = pcw(pc);
     cudaStream_t st = ctx->stream;
-    HISQ_CHECK(loss_and_grad(ctx, pc, fat, naik, mass, reinterpret_cast<const float2 *>(r),
-                             reinterpret_cast<const float2 *>(e), K, st));
+    HISQ_CHECK(loss_and_grad_form(ctx, pc, fat, naik, mass, reinterpret_cast<const float2 *>(r),
+                                  reinterpret_cast<const float2 *>(e), K, st));
     double err2[HISQ_MAX_BUNDLE], e2[HISQ_MAX_BUNDLE];
     HISQ_CUDA(cudaMemcpyAsync(err2, w.err2, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
     HISQ_CUDA(cudaMemcpyAsync(e2, w.r2, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
@@ -667,7 +776,7 @@ int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, do
                     rc = set_error(HISQ_ERR_CUDA, "minibatch gather failed: %s", cudaGetErrorString(ce));
                     break;
                 }
-                rc = loss_and_grad(ctx, pc, fat, naik, mass, rb, eb, batch, st);
+                rc = loss_and_grad_form(ctx, pc, fat, naik, mass, rb, eb, batch, st);
                 if (rc != HISQ_OK) break;
                 step++;
                 pc_adam_kernel<<<(2 * HISQ_PC_WEIGHTS + 255) / 256, 256, 0, st>>>(pc->d_theta, pc->d_m, pc->d_v, w.gbuf,

@@ -331,6 +331,7 @@ struct GraphCache {
     cudaGraph_t graph = nullptr;
     const hisq_links *fat = nullptr, *naik = nullptr;
     const hisq_pc *pc = nullptr;
+    int pc_form = -1;
     double mass = 0;
     int n = 0, prec = -1;
     unsigned tune_generation = 0;
@@ -615,7 +616,7 @@ static int enqueue_iteration_head(const Solve &S) {
 // flexible CG: z = M r (network); beta; p = z + beta p with <p, r>; then the CG head
 static int enqueue_fcg_head(const Solve &S) {
     // the Hermitian part of the network keeps the preconditioned recurrence a true PCG one
-    HISQ_CHECK(pc_forward_hermitian(S.ctx, S.pc, S.fat, S.naik, S.w->r_lo, S.w->z, S.n, S.st));
+    HISQ_CHECK(pc_forward_precond(S.ctx, S.pc, S.fat, S.naik, S.w->r_lo, S.w->z, S.n, S.st));
     HISQ_CHECK(blas(S, HOOK_FCG_BETA));
     HISQ_CHECK(blas(S, HOOK_FCG_PR));
     return enqueue_iteration_head(S);
@@ -738,6 +739,7 @@ static int build_graph(const Solve &S) {
     w->gc.n = S.n;
     w->gc.prec = S.prec;
     w->gc.pc = S.pc;
+    w->gc.pc_form = S.pc ? S.pc->form : -1;
     w->gc.tune_generation = S.ctx->tune_generation;
     return HISQ_OK;
 }
@@ -745,21 +747,22 @@ static int build_graph(const Solve &S) {
 // ------------------------------------------------------------------------------------------
 // Persistent driver: the whole plain-CG solve of a bundle in one cooperative launch
 // ------------------------------------------------------------------------------------------
-static cudaError_t persistent_occ(int prec, int R, size_t smem, int *per_sm) {
+static cudaError_t persistent_occ(int prec, int R, int threads, size_t smem, int *per_sm) {
     switch (prec) {
-    case HISQ_FP64: return persistent_occupancy<HISQ_FP64>(R, smem, per_sm);
-    case HISQ_FP32: return persistent_occupancy<HISQ_FP32>(R, smem, per_sm);
-    case HISQ_FP16: return persistent_occupancy<HISQ_FP16>(R, smem, per_sm);
-    default: return persistent_occupancy<HISQ_BF16>(R, smem, per_sm);
+    case HISQ_FP64: return persistent_occupancy<HISQ_FP64>(R, threads, smem, per_sm);
+    case HISQ_FP32: return persistent_occupancy<HISQ_FP32>(R, threads, smem, per_sm);
+    case HISQ_FP16: return persistent_occupancy<HISQ_FP16>(R, threads, smem, per_sm);
+    default: return persistent_occupancy<HISQ_BF16>(R, threads, smem, per_sm);
     }
 }
 
-static cudaError_t persistent_launch(int prec, const PersArgs &a, int R, int grid, size_t smem, cudaStream_t st) {
+static cudaError_t persistent_launch(int prec, const PersArgs &a, int R, int grid, int threads, size_t smem,
+                                     cudaStream_t st) {
     switch (prec) {
-    case HISQ_FP64: return launch_persistent_prec<HISQ_FP64>(a, R, grid, smem, st);
-    case HISQ_FP32: return launch_persistent_prec<HISQ_FP32>(a, R, grid, smem, st);
-    case HISQ_FP16: return launch_persistent_prec<HISQ_FP16>(a, R, grid, smem, st);
-    default: return launch_persistent_prec<HISQ_BF16>(a, R, grid, smem, st);
+    case HISQ_FP64: return launch_persistent_prec<HISQ_FP64>(a, R, grid, threads, smem, st);
+    case HISQ_FP32: return launch_persistent_prec<HISQ_FP32>(a, R, grid, threads, smem, st);
+    case HISQ_FP16: return launch_persistent_prec<HISQ_FP16>(a, R, grid, threads, smem, st);
+    default: return launch_persistent_prec<HISQ_BF16>(a, R, grid, threads, smem, st);
     }
 }
 
@@ -773,9 +776,13 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     int R = sh.R > 4 ? 4 : sh.R;
     if (S.prec == HISQ_FP64 && R > 2) R = 2;  // four FP64 right-hand sides per thread would spill
     while (S.n % R) R /= 2;
-    const size_t smem = (size_t)(256 * R + 64) * sizeof(double);
+    // block size: the parameter if set (a multiple of 32 up to the kernel's bound), else 512
+    int threads = std::min(pers_threads(R), PERS_DEFAULT_THREADS);
+    const int want = S.ctx->params.persistent_threads;
+    if (want >= 32 && want <= pers_threads(R) && want % 32 == 0) threads = want;
+    const size_t smem = (size_t)(threads * R + 64) * sizeof(double);
     int per_sm = 0;
-    if (persistent_occ(S.prec, R, smem, &per_sm) != cudaSuccess || per_sm < 1) {
+    if (persistent_occ(S.prec, R, threads, smem, &per_sm) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return HISQ_OK;
     }
@@ -821,7 +828,7 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
         HISQ_CUDA(cudaMemsetAsync(w->phase_ns, 0, sizeof(unsigned long long) * 8, S.st));
         HISQ_CUDA(cudaEventRecord(w->ev0, S.st));
     }
-    cudaError_t e = persistent_launch(S.prec, a, R, grid, smem, S.st);
+    cudaError_t e = persistent_launch(S.prec, a, R, grid, threads, smem, S.st);
     if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
         cudaGetLastError();
         return HISQ_OK;  // not co-resident here: the graph driver takes the bundle
@@ -865,6 +872,7 @@ static int solve_bundle(Solve &S, double tol) {
     if (graph) {
         bool reuse = w->gc.exec && w->gc.fat == S.fat && w->gc.naik == S.naik && w->gc.mass == S.mass &&
                      w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == S.pc &&
+                     w->gc.pc_form == (S.pc ? S.pc->form : -1) &&
                      w->gc.tune_generation == S.ctx->tune_generation;
         unsigned long long hl = w->h_st->h_loop, hu = w->h_st->h_upd;
         if (!reuse) {
@@ -948,7 +956,7 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
             return set_error(HISQ_ERR_ARG, "flexible CG with the network needs FP32 inner precision and FP32 links");
         if (P.pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
     }
-    int bundle = P.bundle > 0 ? P.bundle : std::min(nrhs, HISQ_MAX_BUNDLE);
+    int bundle = P.bundle > 0 ? P.bundle : choose_bundle(ctx, fat, naik, nrhs, prec == HISQ_FP64);
     bundle = std::min(bundle, nrhs);
     HISQ_CHECK(ensure_workspace(ctx, bundle, prec, P.pc != nullptr));
     if (P.pc) HISQ_CHECK(pc_prepare(ctx, P.pc, bundle));
@@ -1002,8 +1010,9 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
         // p-update; the three residual-recomputation kernels run when an update is due (graph)
         // or are launched every iteration as gated no-ops (host-driven)
         bool graph_mode = P.use_graph && !S.timing;
-        long per_iter = P.pc ? 3 + 11 + 2 : 4;  // flexible CG: M and M^dag (5 layers each) and their average,
-                                                 // beta and direction kernels
+        // flexible CG adds the network per iteration: M and M^dag (5 layer launches each), plus
+        // their average for the Hermitian part, and the beta and direction kernels
+        long per_iter = !P.pc ? 4 : 3 + (P.pc->form == HISQ_PC_NORMAL ? 10 : 11) + 2;
         if (S.persistent)
             stats.kernel_launches += 3;  // pack b, the persistent solve, unpack x
         else

@@ -205,6 +205,15 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
                 }
             }
         }
+        if (any) {
+            // bundle-wide recomputation: once one right-hand side needs its FP64 residual, all
+            // active ones get it in the same pass.  The FP64 residual Dslash is FP64-arithmetic
+            // bound, so a pass for one of n right-hand sides would cost nearly what a pass for
+            // all n does; updating together also aligns their later triggers (each restarts its
+            // 10x-drop reference here), so a bundle needs about as many passes as one RHS.
+            for (int k = 0; k < n; k++)
+                if (st->active[k]) st->update[k] = 1;
+        }
         st->any_update = any;
         st->update_rounds += any;
         set_condition(st->h_upd, &st->cond_upd, any);

@@ -47,7 +47,8 @@ static int time_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *na
     return rc;
 }
 
-static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64, LaunchShape *best) {
+static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64, LaunchShape *best,
+                     float *best_ms_out) {
     int prec = use64 ? HISQ_FP64 : fat->prec;
     size_t bytes = vector_bytes(prec, ctx->geom.Vh, n);
     void *in = nullptr, *out = nullptr;
@@ -93,6 +94,7 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     cudaFree(in);
     cudaFree(out);
     if (flush) cudaFree(flush);
+    if (best_ms_out) *best_ms_out = best_ms;
     return rc;
 }
 
@@ -107,9 +109,53 @@ LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *
     cudaStreamIsCapturing(ctx->stream, &cs);
     if (cs != cudaStreamCaptureStatusNone) return default_shape(prec, n);
     LaunchShape best;
-    if (run_tuner(ctx, fat, naik, n, use64, &best) != HISQ_OK) best = default_shape(prec, n);
+    float ms = 0.0f;
+    if (run_tuner(ctx, fat, naik, n, use64, &best, &ms) != HISQ_OK) {
+        best = default_shape(prec, n);
+        ms = 0.0f;
+    }
     ctx->tuned[key] = best;
+    if (ms > 0.0f && ms < 1e29f) ctx->tuned_ms[key] = ms;
     ctx->tune_generation++;
+    return best;
+}
+
+// Bundle size for nrhs right-hand sides: the candidate (1, 2, 4, 8, 12, 16 below
+// min(nrhs, 16), and min(nrhs, 16) itself) that
+// minimises the summed tuned Dslash time of the bundles it splits nrhs into (full bundles plus
+// one for the remainder).  Every solver kernel streams the links once per bundle step and the
+// vectors once per right-hand side, as the Dslash does, so its time is the model.  Falls back to
+// the largest bundle when a time is unknown (tuning off or failed).
+int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64) {
+    const int cap = std::min(nrhs, HISQ_MAX_BUNDLE);
+    if (!ctx->params.autotune) return cap;
+    const int prec = use64 ? HISQ_FP64 : fat->prec;
+    const int recon = use64 ? 18 : naik->recon;
+    auto time_of = [&](int n, float *ms) {
+        tuned_shape(ctx, fat, naik, n, use64);
+        auto it = ctx->tuned_ms.find(TuneKey{prec, recon, n, 0});
+        if (it == ctx->tuned_ms.end()) return false;
+        *ms = it->second;
+        return true;
+    };
+    int cands[8], nc = 0;
+    for (int n : {1, 2, 4, 8, 12, 16})
+        if (n < cap) cands[nc++] = n;
+    cands[nc++] = cap;  // one bundle of everything (up to the maximum) is always a candidate
+    int best = cap;
+    double best_t = 1e300;
+    for (int i = 0; i < nc; i++) {
+        const int n = cands[i];
+        float tn = 0.0f, tr = 0.0f;
+        if (!time_of(n, &tn)) return cap;
+        const int full = nrhs / n, rem = nrhs % n;
+        if (rem && !time_of(rem, &tr)) return cap;
+        const double t = (double)full * tn + (rem ? tr : 0.0);
+        if (t < 0.98 * best_t) {  // a larger bundle must be clearly faster (timing noise)
+            best_t = t;
+            best = n;
+        }
+    }
     return best;
 }
 
@@ -127,8 +173,10 @@ extern "C" int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int 
     TuneKey key{fat->prec, naik->recon, nrhs, 0};
     ctx->tuned.erase(key);
     LaunchShape best;
-    HISQ_CHECK(run_tuner(ctx, fat, naik, nrhs, false, &best));
+    float ms = 0.0f;
+    HISQ_CHECK(run_tuner(ctx, fat, naik, nrhs, false, &best, &ms));
     ctx->tuned[key] = best;
+    if (ms > 0.0f && ms < 1e29f) ctx->tuned_ms[key] = ms;
     ctx->tune_generation++;
     if (rhs_per_thread) *rhs_per_thread = best.R;
     if (block_threads) *block_threads = best.threads;

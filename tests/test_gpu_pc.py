@@ -63,6 +63,7 @@ def test_loss_and_gradient_parity(K):
     with gpu(DIMS, 1) as g:
         W = _weights(2, 0.2)
         pc = g.hisq.hisq_pc_create(_as_real(W))
+        g.hisq.hisq_pc_set_form(pc, g.hisq.HISQ_PC_HERMITIAN_PART)  # trained as M itself
         r = np.stack([hi.gaussian_rhs(g.lat, 70 + k) for k in range(K)])
         e = np.stack([hi.gaussian_rhs(g.lat, 90 + k) for k in range(K)])
         grad = np.zeros(2 * NW)
@@ -159,6 +160,7 @@ def test_training_lowers_loss_and_matches_oracle_loss():
         r, e = training_pairs(g, mass, 2, [2, 5, 8, 11, 14, 17, 20, 23])
         rb, eb = pack_pairs(g, r, e)
         pc = g.hisq.hisq_pc_create(_as_real(initial_weights()))
+        g.hisq.hisq_pc_set_form(pc, g.hisq.HISQ_PC_HERMITIAN_PART)
         hist = np.zeros(20)
         g.hisq.hisq_pc_train(pc, g.fat, g.naik, mass, rb, eb, len(r), 16, 20, 1e-2, hist)
         assert hist[-1] < 0.5 * hist[0], hist
@@ -195,15 +197,16 @@ def test_fcg_identity_network_is_cg(graph):
         assert np.all(np.abs(iters - it_cg) <= 2), (iters, it_cg)
 
 
-@pytest.mark.parametrize("graph", [0, 1])
-def test_fcg_with_trained_network_beats_plain_cg_in_iterations(graph):
+@pytest.mark.parametrize("graph,form", [(0, 1), (1, 1), (1, 0)])
+def test_fcg_with_trained_network_beats_plain_cg_in_iterations(graph, form):
     """What the trained network gains: fewer iterations than plain CG to the same FP64 true
-    residual on fresh right-hand sides."""
+    residual on fresh right-hand sides (normal form M^dag M and Hermitian part of M)."""
     mass = 0.05
     with gpu(DIMS, 1) as g:
         r, e = training_pairs(g, mass, 4, list(range(2, 40, 3)))
         rb, eb = pack_pairs(g, r, e)
         pc = g.hisq.hisq_pc_create(_as_real(initial_weights()))
+        g.hisq.hisq_pc_set_form(pc, form)
         g.hisq.hisq_pc_train(pc, g.fat, g.naik, mass, rb, eb, len(r), 16, 60, 1e-2)
         rhs = [hi.gaussian_rhs(g.lat, 400 + k) for k in range(3)]
         x, stats, iters = _fcg(g, pc, rhs, mass, graph)
@@ -245,3 +248,49 @@ def _apply_h(g, pc, v):
     vin, vout = g.pack(v, 1), g.bundle(n, 1)
     g.hisq.hisq_pc_apply_hermitian(pc, g.fat, g.naik, vin, vout, n)
     return g.unpack(vout, n, 1)
+
+
+def _apply_op(g, fn, pc, v):
+    n = len(v)
+    vin, vout = g.pack(v, 1), g.bundle(n, 1)
+    fn(pc, g.fat, g.naik, vin, vout, n)
+    return g.unpack(vout, n, 1)
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_adjoint_and_normal_form_parity(n):
+    """M^dag and M^dag M applied by the GPU against the oracle's adjoint network."""
+    with gpu(DIMS, 1) as g:
+        W = _weights(6, 0.3)
+        pc = g.hisq.hisq_pc_create(_as_real(W))
+        v = np.stack([hi.gaussian_rhs(g.lat, 820 + k) for k in range(n)])
+        adj = _apply_op(g, g.hisq.hisq_pc_apply_adjoint, pc, v)
+        assert rel_err(adj, np.stack([g.oracle.pc_adjoint(W, v[k]) for k in range(n)])) <= 3e-5
+        nrm = _apply_op(g, g.hisq.hisq_pc_apply_normal, pc, v)
+        assert rel_err(nrm, np.stack([g.oracle.pc_normal(W, v[k]) for k in range(n)])) <= 3e-5
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_normal_form_loss_and_gradient_parity(K):
+    """The normal-form loss and its two-term weight gradient against the oracle's."""
+    with gpu(DIMS, 1) as g:
+        W = _weights(7, 0.2)
+        pc = g.hisq.hisq_pc_create(_as_real(W))
+        g.hisq.hisq_pc_set_form(pc, g.hisq.HISQ_PC_NORMAL)
+        r = np.stack([hi.gaussian_rhs(g.lat, 840 + k) for k in range(K)])
+        e = np.stack([hi.gaussian_rhs(g.lat, 860 + k) for k in range(K)])
+        grad = np.zeros(2 * NW)
+        mass = 0.2
+        loss = g.hisq.hisq_pc_loss_grad(pc, g.fat, g.naik, mass, g.pack(r, 1), g.pack(e, 1), K, grad)
+        want_loss, want_grad = g.oracle.pc_loss_grad_normal(W, r, e, mass)
+        assert abs(loss - want_loss) / want_loss <= 1e-5
+        got = grad.view(np.complex128)
+        assert np.linalg.norm(got - want_grad) / np.linalg.norm(want_grad) <= 1e-4
+
+
+def test_set_form_validation():
+    from paper_1409_1510_gb300.hisq import HisqError
+    with gpu((4, 4, 4, 4), 1) as g:
+        pc = g.hisq.hisq_pc_create(None)
+        with pytest.raises(HisqError):
+            g.hisq.hisq_pc_set_form(pc, 7)

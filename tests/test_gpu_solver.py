@@ -140,14 +140,18 @@ def test_plain_fp64_cg_on_lower_precision_links():
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_persistent_matches_graph_iterations(prec):
-    """The persistent kernel runs the same algorithm as the graph driver: same iteration counts
-    and reliable updates, and the FP64 true residual met."""
+    """The persistent kernel runs the same algorithm as the graph driver: the same iteration
+    counts and reliable updates up to rounding, and the FP64 true residual met."""
     dims = (8, 10, 8, 6)
     with gpu(dims, prec) as g:
         rhs = [hi.gaussian_rhs(g.lat, 60 + k) for k in range(4)]
         _, s1, it1, _ = _solve(g, rhs, 0.05, inner_prec=prec, use_graph=1, bundle=4)
         x2, s2, it2, _ = _solve(g, rhs, 0.05, inner_prec=prec, use_graph=2, bundle=4)
-        assert np.array_equal(it1, it2) and s1.reliable_updates == s2.reliable_updates
+        # the persistent kernel forms the direction r + beta p where it is read (16-bit storage
+        # rounds only the stored copy), and sums its dots in another block order
+        slack = 1 if prec < 2 else 3
+        assert np.all(np.abs(it1.astype(int) - it2.astype(int)) <= slack), (it1, it2)
+        assert abs(s1.reliable_updates - s2.reliable_updates) <= len(rhs) * slack
         assert s2.kernel_launches == 3
         true = g.oracle.true_residual(np.stack(rhs), x2, 0.05)
         assert np.all(true <= TOL * SLACK)
@@ -182,4 +186,18 @@ def test_persistent_kernel_timing_and_phases():
         ph = list(s.phase_ms)
         assert all(v >= 0 for v in ph) and ph[0] > 0 and ph[1] > 0 and ph[3] > 0
         assert sum(ph) <= s.solve_kernel_ms * 1.01
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x, 0.05) <= TOL * SLACK)
+
+
+def test_bundle_size_chosen_by_the_autotuner():
+    """bundle = 0: the tuner's split of nrhs into bundles; with autotune off, the largest bundle.
+    Either way every right-hand side reaches the FP64 true residual."""
+    dims = (8, 10, 8, 6)
+    with gpu(dims, 2) as g:
+        rhs = [hi.gaussian_rhs(g.lat, 90 + k) for k in range(6)]
+        x, s, _, res = _solve(g, rhs, 0.05, inner_prec=2, bundle=0)
+        assert s.bundle_size in (1, 2, 4, 6) and s.bundles == -(-6 // s.bundle_size)
+        assert s.converged == 6 and np.all(res <= TOL)
+        x, s, _, res = _solve(g, rhs, 0.05, inner_prec=2, bundle=0, autotune=0)
+        assert s.bundle_size == 6 and s.bundles == 1 and s.converged == 6
         assert np.all(g.oracle.true_residual(np.stack(rhs), x, 0.05) <= TOL * SLACK)

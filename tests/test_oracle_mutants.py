@@ -1,6 +1,7 @@
 """Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the pins catch
 every one of them: a dropped term, a wrong sign, a wrong hop length or site, a transposed
-operand, a wrong mass term and a wrong CG coefficient."""
+operand, a wrong mass term and a wrong CG coefficient, a missing conjugation in the adjoint
+network, a dropped term of the normal-form gradient."""
 import os
 import tempfile
 
@@ -30,6 +31,9 @@ MUTANTS = {
     "cg_beta_inverted": ("double beta = rr_new / rr;", "double beta = rr / rr_new;"),
     "network_adjoint_sign": ("cplx wc = {w[0], -w[1]};", "cplx wc = {w[0], w[1]};"),
     "network_backward_hop_forward": ("long y = hop(L, x, mu, -step);", "long y = hop(L, x, mu, step);"),
+    "network_adjoint_not_conjugated": ("cplx wc = c_conj((cplx){w[0], w[1]});", "cplx wc = (cplx){w[0], w[1]};"),
+    "normal_loss_missing_n_dag_term": ("oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */",
+                                       "/* dropped */"),
 }
 
 
