@@ -563,9 +563,13 @@ def make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, want):
     return rbuf, ebuf, filled * 16
 
 
-def train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, epochs, hist=None):
+def train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, epochs, hist=None, validate=None, rounds=1):
     """Adam on the GPU from the identity plus a 2% random perturbation (the identity is a saddle
-    point); returns the preconditioner handle."""
+    point); returns the preconditioner handle.  With `validate` (a function of the handle that
+    returns the mean flexible-CG iteration count on validation right-hand sides), training runs
+    in `rounds` equal parts and the handle keeps the weights of the best validated part (the
+    residual-norm loss does not see the conditioning of the preconditioned operator, which can
+    drift while the loss stays flat); returns (handle, validation curve) then."""
     rng = np.random.default_rng(0)
     w0 = np.zeros(408, complex)
     w0[[0, 68, 340]] = 1.0
@@ -573,9 +577,25 @@ def train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, epochs, hist
     pc = hisq.hisq_pc_create(np.ascontiguousarray(w0).view(np.float64))
     if hist is None:
         hist = np.zeros(epochs)
-    hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, npairs, 16, epochs, 5e-3, hist)
+    if validate is None:
+        hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, npairs, 16, epochs, 5e-3, hist)
+        torch.cuda.synchronize()
+        return pc
+    per = max(1, epochs // rounds)
+    curve, best, best_w = [], None, None
+    for k in range(0, epochs, per):
+        h = np.zeros(min(per, epochs - k))
+        hisq.hisq_pc_train(pc, fat, naik, mass, rbuf, ebuf, npairs, 16, len(h), 5e-3, h)
+        hist[k:k + len(h)] = h
+        its = validate(pc)
+        curve.append({"epochs": k + len(h), "loss": float(h[-1]), "validation_iterations": its})
+        print(f"training: {curve[-1]}", file=sys.stderr, flush=True)
+        if best is None or its < best:
+            best, best_w = its, np.zeros(2 * 408)
+            hisq.hisq_pc_get_weights(pc, best_w)
+    hisq.hisq_pc_set_weights(pc, best_w)
     torch.cuda.synchronize()
-    return pc
+    return pc, curve
 
 
 def run_learned(args):
@@ -596,9 +616,22 @@ def run_learned(args):
     t0 = time.perf_counter()
     rbuf, ebuf, pairs = make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, args.pairs)
     t_pairs = time.perf_counter() - t0
+    print(f"pairs: {pairs} in {t_pairs:.1f} s", file=sys.stderr, flush=True)
     hist = np.zeros(args.epochs)
+    valid = [d64(hi.gaussian_rhs(lat, 8000 + k)) for k in range(16)]
+    # flexible CG gets at most ten times the iterations plain CG needs (a poor network then ends
+    # unconverged, and is reported as such, instead of running to the default limit)
+    _, _, its_cg, _ = _solve_set(hisq, torch, fat, naik, valid, mass, inner_prec=1, bundle=16)
+    cap = int(10 * its_cg.max())
+
+    def validate(handle):
+        _, st, its, _ = _solve_set(hisq, torch, fat, naik, valid, mass, inner_prec=1, bundle=16, pc=handle.value,
+                                   max_iter=cap)
+        return float(its.mean()) if st.converged == len(valid) else float(cap)
+
     t0 = time.perf_counter()
-    pc = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, pairs, args.epochs, hist)
+    pc, curve = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, pairs, args.epochs, hist, validate,
+                              rounds=6)
     t_train = time.perf_counter() - t0
     # fresh right-hand sides: plain CG against flexible CG with the network (both FP32 inner,
     # FP64 reliable updates, true residual 1e-10 judged in FP64)
@@ -606,14 +639,17 @@ def run_learned(args):
     out = {}
     for name, handle in (("cg", None), ("fcg_learned", pc)):
         hv = handle.value if handle is not None else None
-        _solve_set(hisq, torch, fat, naik, tests[:16], mass, inner_prec=1, bundle=16, pc=hv)  # warm-up
-        sec, st, iters, res = _solve_set(hisq, torch, fat, naik, tests, mass, inner_prec=1, bundle=16, pc=hv)
+        _solve_set(hisq, torch, fat, naik, tests[:16], mass, inner_prec=1, bundle=16, pc=hv, max_iter=cap)  # warm-up
+        sec, st, iters, res = _solve_set(hisq, torch, fat, naik, tests, mass, inner_prec=1, bundle=16, pc=hv,
+                                         max_iter=cap)
         out[name] = {"s_per_rhs": sec / len(tests), "mean_iterations": float(iters.mean()),
                      "max_true_residual": float(res.max()), "converged": st.converged,
                      "fallbacks": st.fallbacks}
+        print(f"test {name}: {out[name]}", file=sys.stderr, flush=True)
     line = {"mode": "learned", "lattice": dims, "mass": mass, "pairs": pairs, "pair_seconds": t_pairs,
             "train_seconds": t_train, "epochs": args.epochs, "loss_first": float(hist[0]),
-            "loss_last": float(hist[-1]), "test_rhs": len(tests), **out,
+            "loss_last": float(hist[-1]), "form": "normal (M^dag M)", "validation": curve, "max_iter": cap,
+            "validation_rhs": len(valid), "test_rhs": len(tests), **out,
             "iteration_ratio": out["fcg_learned"]["mean_iterations"] / out["cg"]["mean_iterations"],
             "time_ratio": out["fcg_learned"]["s_per_rhs"] / out["cg"]["s_per_rhs"]}
     print(json.dumps(line), flush=True)
@@ -632,7 +668,8 @@ def _solve_set(hisq, torch, fat, naik, bs, mass, **params):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    hisq.hisq_cg_solve(fat, naik, bs, xs, mass, TOL)
+    # a right-hand side that misses tol within max_iter is reported through the stats
+    hisq.hisq_cg_solve(fat, naik, bs, xs, mass, TOL, raise_on_error=False)
     e1.record(stream)
     e1.synchronize()
     iters = np.zeros(len(bs), dtype=np.int32)
@@ -762,14 +799,24 @@ def production_pc(args, hisq, torch, hi, lat, X, N, mass, d64):
     naik = hisq.hisq_links_create(d64(N), True, 1, 18)
     pairs = make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, args.pairs)
     rbuf, ebuf, npairs = pairs
-    pc = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, args.epochs)
+    valid = [d64(hi.z2_rhs(lat, 59000 + k)) for k in range(16)]
+    _, _, its_cg, _ = _solve_set(hisq, torch, fat, naik, valid, mass, inner_prec=1, bundle=16)
+    cap = int(10 * its_cg.max())
+
+    def validate(handle):
+        _, st, its, _ = _solve_set(hisq, torch, fat, naik, valid, mass, inner_prec=1, bundle=16, pc=handle.value,
+                                   max_iter=cap)
+        return float(its.mean()) if st.converged == len(valid) else float(cap)
+
+    pc, curve = train_network(hisq, torch, fat, naik, mass, rbuf, ebuf, npairs, args.epochs, None, validate,
+                              rounds=max(1, min(args.epochs, 4)))
     sample = [d64(hi.z2_rhs(lat, 60000 + k)) for k in range(args.test_rhs)]
-    out = {"pairs": npairs, "epochs": args.epochs}
+    out = {"pairs": npairs, "epochs": args.epochs, "validation": curve}
     for name, handle in (("cg", None), ("fcg_learned", pc)):
         _solve_set(hisq, torch, fat, naik, sample[:16], mass, inner_prec=1, bundle=16,
-                   pc=handle.value if handle is not None else None)
+                   pc=handle.value if handle is not None else None, max_iter=cap)
         sec, st, iters, res = _solve_set(hisq, torch, fat, naik, sample, mass, inner_prec=1, bundle=16,
-                                         pc=handle.value if handle is not None else None)
+                                         pc=handle.value if handle is not None else None, max_iter=cap)
         out[name] = {"s_per_rhs": sec / len(sample), "mean_iterations": float(iters.mean()),
                      "max_true_residual": float(res.max()), "converged": int(st.converged),
                      "fallbacks": int(st.fallbacks)}

@@ -80,6 +80,12 @@ int hisq_init(const int dims[4], int device, void *cuda_stream);
  * workspace, captured graphs). */
 int hisq_finalize(void);
 
+/* Synchronise the context's stream and report whether a bounded device-side wait ran out since
+ * the last call (HISQ_ERR_TIMEOUT; the output of that launch is invalid and the flag is
+ * cleared), else HISQ_OK.  The staged Dslash waits for its tiles' bulk copies with such a
+ * bound, so a lost transfer ends the kernel instead of hanging it. */
+int hisq_device_status(void);
+
 const char *hisq_strerror(int status);
 const char *hisq_last_error(void);
 
@@ -181,6 +187,11 @@ typedef struct {
     int persistent_threads; /* block size of the persistent solve kernel: 0 = 512; otherwise a
                              multiple of 32 up to 1024 (one right-hand side per thread) or 512;
                              the grid is every block that fits on the GPU at once */
+    int single_reduction; /* persistent driver: 1 (default) single-reduction CG (Chronopoulos &
+                             Gear 1989: |r|^2 and <r, A r> in one reduction, q = A p by recurrence;
+                             three grid barriers an iteration; not with BF16 storage, whose
+                             rounding breaks the recurrence for <p, A p>), 0 Hestenes-Stiefel
+                             (two reductions, four barriers) as in the other drivers */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);
@@ -232,8 +243,9 @@ int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual)
 /* Pick and cache the fastest Dslash launch shape for nrhs right-hand sides in the links'
  * precision, timing every candidate with CUDA events after an L2 flush.  Writes the
  * chosen right-hand sides per thread, threads per block and lanes per site (1; 2 when the fat
- * and Naik halves of a site run on two lanes; 4 when each lane takes two directions of one kind)
- * if the pointers are not NULL.  Allocates its
+ * and Naik halves of a site run on two lanes; 4 when each lane takes two directions of one kind;
+ * 8 for that split with staged link records, see hisq_set_launch_shape) if the pointers are not
+ * NULL.  Allocates its
  * timing buffers. */
 int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int nrhs, int *rhs_per_thread,
                   int *block_threads, int *lanes_per_site);
@@ -241,7 +253,9 @@ int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int nrhs, int *
 /* Pin the Dslash launch shape used for nrhs right-hand sides with links of (prec, recon):
  * rhs_per_thread in {1, 2, 4, 8} dividing nrhs (FP64: 1, 2, 4), block_threads in 32..256,
  * lanes_per_site 1, 2 (18-real Naik links, rhs_per_thread <= 4) or 4 (18-real Naik links,
- * rhs_per_thread <= 2).
+ * rhs_per_thread <= 2), or 8: the four-lane split with each tile's link records staged in shared
+ * memory by the bulk-copy engine (18-real Naik, FP32/FP16/BF16, rhs_per_thread <= 2; tiles of
+ * block_threads / (4 nrhs / rhs_per_thread) sites, block_threads up to 512).
  * Overrides the autotuner's choice for that key. */
 int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_thread, int block_threads,
                           int lanes_per_site);
@@ -303,7 +317,9 @@ int hisq_pc_adam_step(hisq_pc *pc, const double *grad, int step, double lr, doub
 /* Train on K pairs (device FP32 internal, stored as ceil(K/16) consecutive bundles of 16
  * vectors, the last one padded) for `epochs` passes of minibatches of `batch` (<= 16) pairs
  * with Adam at learning rate lr, on the loss of hisq_pc_loss_grad.  loss_history (host, epochs
- * doubles, may be NULL) receives the mean loss of each epoch. */
+ * doubles, may be NULL) receives the mean loss of each epoch.  Consecutive calls continue one
+ * Adam run (moments and step count kept in the handle; hisq_pc_set_weights starts a new one),
+ * so training can be interleaved with validation solves. */
 int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, double mass,
                   const void *r, const void *e, int K, int batch, int epochs, double lr,
                   double *loss_history);

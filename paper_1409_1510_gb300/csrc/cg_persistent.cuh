@@ -19,7 +19,8 @@ struct PersArgs {
     Geom g;
     LinkField fat, naik;      // inner precision (18-real Naik)
     LinkField fat64, naik64;  // FP64 copies
-    void *p, *t, *ap;         // inner precision bundles
+    void *p, *t, *ap;         // inner precision bundles (ap: A p, or A r = s in single-reduction CG)
+    void *q, *rp;             // single-reduction CG: q = A p and r in the storage precision
     void *x, *r;              // x_lo and r in the iterated precision
     void *b, *xhi, *t64;      // FP64
     double mass2;
@@ -120,13 +121,13 @@ __device__ __forceinline__ int tile_sites(int count, int spb) {
     return min(spb, (count + (int)gridDim.x - 1) / (int)gridDim.x);
 }
 
-// Per-block column sums of the threads' dots into partials[blockIdx.x][*].  Thread
+// Per-block column sums of the threads' dots into partials[blockIdx.x][col0 + *].  Thread
 // tid = site_row * t + gi holds dot[r] of column gi * R + r (ndots = t * R columns).  With t a
 // power of two the lanes of one column meet in a shuffle tree and the warps' sums in one more
 // step; otherwise the dots go through red[rows][ndots] (red holds blockDim.x * R doubles).
 template <int R>
 __device__ __forceinline__ void publish_dots(const PersArgs &a, double *red, double (&dot)[R], int t, int gi,
-                                             int ndots) {
+                                             int ndots, int col0 = 0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     __syncthreads();  // red may still be read by the previous step
     if ((t & (t - 1)) == 0 && t <= 32) {
@@ -143,7 +144,7 @@ __device__ __forceinline__ void publish_dots(const PersArgs &a, double *red, dou
             double s = lane < nwarps ? red[lane * ndots + j] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + col0 + j] = s;
         }
         return;
     }
@@ -159,6 +160,56 @@ __device__ __forceinline__ void publish_dots(const PersArgs &a, double *red, dou
     for (int j = warp; j < ndots; j += nwarps) {
         double s = 0.0;
         for (int q = lane; q < rows; q += 32) s += red[q * ndots + j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + col0 + j] = s;
+    }
+}
+
+// The same for two sets of dots in one pass: dot[k][r] is column k n + gi R + r (n = t R); red
+// holds 2 blockDim.x * R doubles.
+template <int R>
+__device__ __forceinline__ void publish_dots2(const PersArgs &a, double *red, double (&dot)[2][R], int t, int gi,
+                                              int n) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nd = 2 * n;
+    __syncthreads();  // red may still be read by the previous step
+    if ((t & (t - 1)) == 0 && t <= 32) {
+        for (int off = 16; off >= t; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+#pragma unroll
+                for (int r = 0; r < R; r++) dot[k][r] += __shfl_xor_sync(0xffffffffu, dot[k][r], off);
+        if (lane < t) {
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (gi * R + r < n) red[warp * nd + k * n + gi * R + r] = dot[k][r];
+        }
+        __syncthreads();
+        for (int j = warp; j < nd; j += nwarps) {
+            double s = lane < nwarps ? red[lane * nd + j] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+        }
+        return;
+    }
+    const int rows = blockDim.x / t, row = tid / t;
+    for (int i = tid; i < rows * nd; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    if (row < rows) {
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (gi * R + r < n) red[row * nd + k * n + gi * R + r] = dot[k][r];
+    }
+    __syncthreads();
+    for (int j = warp; j < nd; j += nwarps) {
+        double s = 0.0;
+        for (int q = lane; q < rows; q += 32) s += red[q * nd + j];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
@@ -194,12 +245,14 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
 
 // One Dslash phase over the block's share of the sites of output parity `parity`, input from the
 // loader `in`.  EPI_PLAIN: out = D in.  EPI_AOP: out = m^2 ax - D in with Re<ax, out> per block
-// (ax from the loader `ax` at the output site).  EPI_RESID (FP64): r = b - m^2 ax + D in, written
-// to out_lo (iterated precision Q) with |r|^2 per block.  mask[r] selects right-hand sides.
-template <int PP, int R, int EPI, int Q, class IN, class AX>
+// (ax from the loader `ax` at the output site); with DOTS2 also |ax|^2, published as the first n
+// columns (Re<ax, out> then follows as columns n..2n-1).  EPI_RESID (FP64): r = b - m^2 ax + D in,
+// written to out_lo (iterated precision Q), and to out_p (storage precision P) if given, with
+// |r|^2 per block.  mask[r] selects right-hand sides.
+template <int PP, int R, int EPI, int Q, class IN, class AX, bool DOTS2 = false, int P = PP>
 __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
                                              const IN &in, void *out, int parity, const int *mask, const AX &ax,
-                                             const void *bvec, void *out_lo, double *red) {
+                                             const void *bvec, void *out_lo, double *red, void *out_p = nullptr) {
     using real = typename Prec<PP>::real;
     const Geom &g = a.g;
     const int n = a.n, t = n / R, spb = blockDim.x / t;
@@ -212,9 +265,9 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
         act[r] = r0 + r < n && mask[r0 + r] != 0;
         any |= act[r];
     }
-    double dot[R];
+    double dot[R], dot2[R];  // Re<ax, out>; |ax|^2 (DOTS2)
 #pragma unroll
-    for (int r = 0; r < R; r++) dot[r] = 0.0;
+    for (int r = 0; r < R; r++) dot[r] = dot2[r] = 0.0;
     const int ts = tile_sites(g.Vh, spb);
     if (any && sl < ts) {
         for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
@@ -234,13 +287,15 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                 for (int r = 0; r < R; r++) {
                     if (!act[r]) continue;
                     Cplx<real> w[3];
-                    real d = 0;
+                    real d = 0, d2 = 0;
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         w[c] = {m2 * p[r][c].re - acc[r][c].re, m2 * p[r][c].im - acc[r][c].im};
                         d += p[r][c].re * w[c].re + p[r][c].im * w[c].im;
+                        if constexpr (DOTS2) d2 += p[r][c].re * p[r][c].re + p[r][c].im * p[r][c].im;
                     }
                     dot[r] += (double)d;
+                    if constexpr (DOTS2) dot2[r] += (double)d2;
                     store_vec<PP>(vout, s, r0 + r, w);
                 }
             } else {
@@ -265,20 +320,38 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                     }
                     dot[r] += d;
                     store_vec<Q>(vlo, s, r0 + r, lo3);
+                    if (out_p) {
+                        Cplx<typename Prec<P>::real> lp[3];
+#pragma unroll
+                        for (int c = 0; c < 3; c++)
+                            lp[c] = {(typename Prec<P>::real)lo3[c].re, (typename Prec<P>::real)lo3[c].im};
+                        store_vec<P>(VecView<P>{out_p, n}, s, r0 + r, lp);
+                    }
                 }
             }
         }
     }
-    if constexpr (EPI != EPI_PLAIN) publish_dots<R>(a, red, dot, t, gi, n);
+    if constexpr (DOTS2) {
+        double both[2][R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            both[0][r] = dot2[r];
+            both[1][r] = dot[r];
+        }
+        publish_dots2<R>(a, red, both, t, gi, n);
+    } else if constexpr (EPI != EPI_PLAIN) {
+        publish_dots<R>(a, red, dot, t, gi, n);
+    }
 }
 
 // the solve loop (body in cg_persistent_body.cuh, instantiated per precision)
-template <int P, int R>
+template <int P, int R, bool CG1>
 __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const __grid_constant__ PersArgs a);
 
 template <int P>
-cudaError_t launch_persistent_prec(const PersArgs &a, int R, int grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_persistent_prec(const PersArgs &a, int R, bool cg1, int grid, int threads, size_t smem,
+                                   cudaStream_t st);
 template <int P>
-cudaError_t persistent_occupancy(int R, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t persistent_occupancy(int R, bool cg1, int threads, size_t smem, int *blocks_per_sm);
 
 }  // namespace hisq

@@ -321,13 +321,22 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int S = 1;
     if (recon == 18 && sh.S == 2 && R <= 4) S = 2;
     if (recon == 18 && sh.S == 4 && R <= 2) S = 4;
+    if (recon == 18 && sh.S == 8 && R <= 2 && prec != HISQ_FP64 && d.epi != EPI_RESID) S = 8;
     int t = (d.n + R - 1) / R;
     // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
     // threads keep both the partial count and that block's share of the sum small
     int want_threads = d.epi != EPI_PLAIN ? std::max(sh.threads, 128) : sh.threads;
-    int spb = pow2_floor(std::max(1, std::min(want_threads, 256) / (S * t)));  // kernels are bounded to 256 threads
-    int threads = (spb * S * t + 31) / 32 * 32;  // whole warps; threads with site index >= spb idle
-    if (threads > 256) return set_error(HISQ_ERR_ARG, "launch shape of %d threads is too large", threads);
+    int spb, threads;
+    if (S == 8) {
+        // staged: threads = 4 t TS exactly (TS sites per tile), up to 512
+        spb = std::max(1, std::min(sh.threads, 512) / (4 * t));
+        threads = 4 * t * spb;
+        if (threads % 32) return set_error(HISQ_ERR_ARG, "staged launch shape of %d threads is not whole warps", threads);
+    } else {
+        spb = pow2_floor(std::max(1, std::min(want_threads, 256) / (S * t)));  // kernels are bounded to 256 threads
+        threads = (spb * S * t + 31) / 32 * 32;  // whole warps; threads with site index >= spb idle
+        if (threads > 256) return set_error(HISQ_ERR_ARG, "launch shape of %d threads is too large", threads);
+    }
 
     KArgs a;
     memset(&a, 0, sizeof(a));
@@ -353,9 +362,16 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     a.red.hook = d.hook;
     a.red.st = reinterpret_cast<SolverState *>(d.hook_state);
     a.red.partials_only = d.partials_only;
+    a.err = ctx->dev_err;
 
     size_t smem = 0;
-    if (d.epi != EPI_PLAIN) {
+    if (S == 8) {
+        smem = staged_smem(a.fat.W + a.naik.W, spb, threads, d.n, d.epi != EPI_PLAIN);
+        if (smem > 227 * 1024)
+            return set_error(HISQ_ERR_ARG, "staged launch shape needs %zu bytes of shared memory", smem);
+        if (d.epi != EPI_PLAIN && (!d.partials || !d.counter || (size_t)ctx->num_sms * 8 * d.n > d.partials_cap))
+            return set_error(HISQ_ERR_ARG, "reduction scratch too small for the Dslash epilogue");
+    } else if (d.epi != EPI_PLAIN) {
         size_t need = std::max((size_t)spb * d.n, (size_t)threads + 64);
         smem = need * sizeof(double);
         long tiles = (ctx->geom.Vh + spb - 1) / spb;
@@ -427,6 +443,7 @@ void hisq_default_solver_params(hisq_solver_params *p) {
     p->stall_factor = 10.0;
     p->autotune = 1;
     p->time_kernels = 0;
+    p->single_reduction = 1;
 }
 
 int hisq_init(const int dims[4], int device, void *cuda_stream) {
@@ -463,12 +480,29 @@ int hisq_init(const int dims[4], int device, void *cuda_stream) {
     ctx->num_sms = prop.multiProcessorCount;
     hisq_default_solver_params(&ctx->params);
     if (cudaMalloc(&ctx->counter, sizeof(unsigned int) * 4) != cudaSuccess ||
-        cudaMalloc(&ctx->dot_out, sizeof(double) * HISQ_MAX_NRHS * 4) != cudaSuccess) {
+        cudaMalloc(&ctx->dot_out, sizeof(double) * HISQ_MAX_NRHS * 4) != cudaSuccess ||
+        cudaMalloc(&ctx->dev_err, sizeof(int) * 4) != cudaSuccess) {
+        if (ctx->counter) cudaFree(ctx->counter);
+        if (ctx->dot_out) cudaFree(ctx->dot_out);
         delete ctx;
         return set_error(HISQ_ERR_NOMEM, "context scratch allocation failed");
     }
     cudaMemset(ctx->counter, 0, sizeof(unsigned int) * 4);
+    cudaMemset(ctx->dev_err, 0, sizeof(int) * 4);
     g_ctx = ctx;
+    return HISQ_OK;
+}
+
+int hisq_device_status(void) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    int flag = 0;
+    HISQ_CUDA(cudaMemcpy(&flag, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        HISQ_CUDA(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+        return set_error(HISQ_ERR_TIMEOUT, "a bounded device wait (staged Dslash tile) ran out; its output is invalid");
+    }
     return HISQ_OK;
 }
 
@@ -499,6 +533,7 @@ int hisq_finalize(void) {
     if (ctx->tmp) cudaFree(ctx->tmp);
     if (ctx->counter) cudaFree(ctx->counter);
     if (ctx->dot_out) cudaFree(ctx->dot_out);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     delete ctx;
     g_ctx = nullptr;
     return HISQ_OK;

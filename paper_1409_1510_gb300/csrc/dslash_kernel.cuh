@@ -14,6 +14,7 @@
 #include "hisq_internal.cuh"
 #include "link_codec.cuh"
 #include "solver_state.cuh"
+#include "bulk_copy.cuh"
 
 namespace hisq {
 
@@ -41,6 +42,7 @@ struct KArgs {
     const int *active;
     const int *gate;
     RedArgs red;
+    int *err;        // staged kernel: set when a bounded wait for a staged tile runs out
 };
 
 template <int P>
@@ -429,6 +431,190 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
         }
         // every thread reaches the reduction (idle threads contributed zeros)
         block_reduce_finish(red, a.spb, a.n, a.n, a.red);
+    }
+}
+
+// ---- staged variant: link records of a tile of sites brought into shared memory in bulk ----
+//
+// The link records of TS consecutive output sites form, for every 16-byte word plane j of the
+// gathered layout, one contiguous run of TS words; a single thread copies the W_X + W_N runs of a
+// tile with the bulk-copy engine into a shared-memory stage while the block computes on the other
+// stage (two stages).  Memory parallelism then no longer depends on how many link loads each
+// thread can keep in flight, which at one right-hand side and a few hundred sites per SM is what
+// limits the plain kernel.  Four lanes share a site as in the S = 4 split (two directions of one
+// link kind per lane); neighbour vectors are read from global memory (they are reused by 16 sites
+// and mostly hit in L2).  18-real Naik records only.
+
+// words of the gathered records per site: fat then Naik planes; stage k holds (W_X + W_N) * TS
+// words, plane j at [j * TS, (j + 1) * TS)
+template <int P, int R, bool COHERENT>
+__device__ __forceinline__ void staged_stencil(const Geom &g, const LinkField &fat_f, const LinkField &naik_f,
+                                               int parity, const uint4 *stage, int TS, int sl,
+                                               const PlainIn<P, COHERENT> &vin, int s, int part, int r0,
+                                               const bool act[R], Cplx<typename Prec<P>::real> acc[R][3]) {
+    using real = typename Prec<P>::real;
+    using C = LinkCodec<P, 18>;
+    constexpr bool SCALED = (P == HISQ_FP16 || P == HISQ_BF16);
+    const SiteCoord sc = decode_site(g, s, parity);
+    const bool naik_kind = (part >> 1) != 0;
+    const int half = part & 1;
+    const int hop = naik_kind ? 3 : 1;
+    const int plane0 = naik_kind ? fat_f.W : 0;
+    constexpr int GPH = 4 / C::G;  // groups per half record (4 links)
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
+#pragma unroll
+    for (int gg = 0; gg < GPH; gg++) {
+        uint32_t u[C::WG * 4];
+        const int w0 = plane0 + (half * GPH + gg) * C::WG;
+#pragma unroll
+        for (int j = 0; j < C::WG; j++) {
+            const uint4 w = stage[(size_t)(w0 + j) * TS + sl];
+            u[4 * j] = w.x; u[4 * j + 1] = w.y; u[4 * j + 2] = w.z; u[4 * j + 3] = w.w;
+        }
+#pragma unroll
+        for (int l = 0; l < C::G; l++) {
+            const int j = gg * C::G + l;
+            const int nb = neighbour_rt(g, sc, s, 2 * half + (j >> 1), (j & 1) ? -hop : hop);
+            Cplx<real> M[3][3];
+            C::decode(u, l, M);
+            Cplx<real> v[R][3];
+            vin.template load<R>(nb, r0, act, v);
+            matvec_acc<real, R>(M, v, acc);
+        }
+    }
+    if constexpr (SCALED) {
+        const LinkField &f = naik_kind ? naik_f : fat_f;
+        scale_acc<real, R>(acc, (real)__ldg(f.scale + (size_t)parity * g.Vh + s));
+    }
+}
+
+constexpr long STAGE_WAIT_LIMIT = 1L << 22;  // bounded wait for a staged tile (about a second)
+
+template <int P, int R, int EPI>
+__global__ void __launch_bounds__(512, 1) dslash_staged_kernel(KArgs a) {
+    using real = typename Prec<P>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.gate && *a.gate == 0) return;
+    const Geom &g = a.g;
+    const int tid = threadIdx.x;
+    const int part = tid & 3;
+    const int gi = (tid >> 2) % a.t;
+    const int sl = tid / (4 * a.t);
+    const int TS = a.spb;  // sites per tile
+    const int r0 = gi * R;
+    const int nvalid = min(R, a.n - r0);
+    const int Wt = a.fat.W + a.naik.W;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    uint4 *stages = reinterpret_cast<uint4 *>(smem_raw + 16);
+    double *red = reinterpret_cast<double *>(smem_raw + 16 + (size_t)2 * Wt * TS * sizeof(uint4));
+    const PlainIn<P, false> vin{view<P>(a.in, g.Vh, a.n)};
+    const VecView<P> vout = view<P>(a.out, g.Vh, a.n);
+
+    bool act[R];
+    bool any_act = false;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        act[r] = (r < nvalid) && (a.active == nullptr || a.active[r0 + r] != 0);
+        any_act |= act[r];
+    }
+    double dot[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) dot[r] = 0.0;
+
+    const int tiles = (g.Vh + TS - 1) / TS;
+    // thread 0 copies tile k of this block (tile index blockIdx.x + k * gridDim.x) into stage k & 1
+    auto issue = [&](int k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= tiles) return;
+        const int s0 = tile * TS, ns = min(TS, g.Vh - s0);
+        const uint32_t bytes = (uint32_t)ns * sizeof(uint4);
+        uint64_t *b = bar + (k & 1);
+        uint4 *dst = stages + (size_t)(k & 1) * Wt * TS;
+        mbar_arrive_expect(b, bytes * (uint32_t)Wt);
+        for (int j = 0; j < a.fat.W; j++)
+            bulk_copy_g2s(dst + (size_t)j * TS, a.fat.words + ((size_t)a.parity * a.fat.W + j) * g.Vh + s0, bytes, b);
+        for (int j = 0; j < a.naik.W; j++)
+            bulk_copy_g2s(dst + (size_t)(a.fat.W + j) * TS,
+                          a.naik.words + ((size_t)a.parity * a.naik.W + j) * g.Vh + s0, bytes, b);
+    };
+    __shared__ int s_ok;
+    if (tid == 0) {
+        s_ok = 1;
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        issue(0);
+        issue(1);
+    }
+    for (int k = 0; blockIdx.x + k * (int)gridDim.x < tiles; k++) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        const int s = tile * TS + sl;
+        // every thread waits on the stage (bounded); a wait that runs out is recorded and the
+        // tile is skipped, so the kernel always ends
+        const bool ready = mbar_wait(bar + (k & 1), (uint32_t)((k >> 1) & 1), STAGE_WAIT_LIMIT);
+        if (!ready) s_ok = 0;
+        const bool valid = ready && sl < TS && s < g.Vh && any_act;
+        Cplx<real> acc[R][3];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[r][c] = {0, 0};
+        if (valid)
+            staged_stencil<P, R, false>(g, a.fat, a.naik, a.parity, stages + (size_t)(k & 1) * Wt * TS, TS, sl, vin, s,
+                                        part, r0, act, acc);
+#pragma unroll
+        for (int off = 1; off < 4; off <<= 1)
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    acc[r][c].re += __shfl_xor_sync(0xffffffffu, acc[r][c].re, off);
+                    acc[r][c].im += __shfl_xor_sync(0xffffffffu, acc[r][c].im, off);
+                }
+        if (valid && part == 0) {
+            if constexpr (EPI == EPI_PLAIN) {
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (act[r]) store_vec<P>(vout, s, r0 + r, acc[r]);
+            } else {
+                static_assert(EPI == EPI_AOP, "the staged kernel has the plain and A-operator epilogues");
+                const VecView<P> vp = view<P>(a.axpy, g.Vh, a.n);
+                const real m2 = (real)a.mass2;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    if (!act[r]) continue;
+                    Cplx<real> p[3], w[3];
+                    load_vec<P>(vp, s, r0 + r, p);
+                    real d = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        w[c] = {m2 * p[c].re - acc[r][c].re, m2 * p[c].im - acc[r][c].im};
+                        d += p[c].re * w[c].re + p[c].im * w[c].im;
+                    }
+                    dot[r] += (double)d;
+                    store_vec<P>(vout, s, r0 + r, w);
+                }
+            }
+        }
+        __syncthreads();  // the stage is free again
+        if (tid == 0) issue(k + 2);
+    }
+    if (tid == 0 && !s_ok && a.err) atomicExch(a.err, 1);
+    if constexpr (EPI != EPI_PLAIN) {
+        for (int i = tid; i < TS * a.n; i += blockDim.x) red[i] = 0.0;
+        __syncthreads();
+        if (sl < TS && part == 0) {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (r < nvalid) red[sl * a.n + r0 + r] = dot[r];
+        }
+        block_reduce_finish(red, TS, a.n, a.n, a.red);
     }
 }
 

@@ -33,8 +33,29 @@ inline cudaError_t launch_one(const KArgs &a, int threads, size_t smem, int num_
     return cudaGetLastError();
 }
 
+// The staged kernel (S = 8: four lanes per site, link records of a tile staged in shared memory
+// by the bulk-copy engine); one launch shape = sites per tile a.spb, threads = 4 t a.spb.
+template <int P, int R, int EPI>
+inline cudaError_t launch_staged(const KArgs &a, int threads, size_t smem, int num_sms, cudaStream_t stream,
+                                 int *grid_out) {
+    auto k = dslash_staged_kernel<P, R, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    long tiles = (a.g.Vh + a.spb - 1) / a.spb;
+    int grid = wave_grid(k, threads, smem, num_sms, tiles);
+    if (grid_out) *grid_out = grid;
+    k<<<grid, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P, int NR, int EPI>
 inline cudaError_t launch_r(const KArgs &a, int R, int S, int threads, size_t smem, int num_sms, cudaStream_t s, int *grid) {
+    if constexpr (NR == 18 && P != HISQ_FP64 && EPI != EPI_RESID) {
+        if (S == 8) {
+            if (R == 1) return launch_staged<P, 1, EPI>(a, threads, smem, num_sms, s, grid);
+            return launch_staged<P, 2, EPI>(a, threads, smem, num_sms, s, grid);
+        }
+    }
     if constexpr (NR == 18) {
         if (S == 4) {
             if (R == 1) return launch_one<P, NR, 1, EPI, 4>(a, threads, smem, num_sms, s, grid);

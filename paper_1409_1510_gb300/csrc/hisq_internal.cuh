@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 #include <map>
+#include <algorithm>
 
 #include "../../include/hisq.h"
 
@@ -225,6 +226,7 @@ struct hisq_pc {
     double *d_theta, *d_m, *d_v;           // Adam state on the device (FP64, real parameters)
     void *work;                            // network workspace (pc.cu)
     int form;                              // HISQ_PC_NORMAL or HISQ_PC_HERMITIAN_PART
+    int train_steps;                       // Adam steps taken by hisq_pc_train (continued across calls)
 };
 
 namespace hisq {
@@ -242,8 +244,17 @@ struct TuneKey {
 struct LaunchShape {
     int R;        // right-hand sides per thread
     int threads;  // threads per block
-    int S = 1;    // lanes per (site, rhs group): 2 splits the fat and Naik halves (18-real Naik)
+    int S = 1;    // lanes per (site, rhs group): 2 splits the fat and Naik halves, 4 two directions
+                  // of one kind per lane (18-real Naik); 8 = the 4-lane split with the tile's link
+                  // records staged in shared memory by the bulk-copy engine
 };
+
+// shared memory of the staged kernel for TS sites per tile: two stages of link records, the
+// mbarriers, and the reduction scratch of the reducing epilogue
+inline size_t staged_smem(int words_per_site, int TS, int threads, int n, bool reducing) {
+    size_t red = reducing ? std::max((size_t)TS * n, (size_t)threads + 64) * sizeof(double) : 0;
+    return 16 + (size_t)2 * words_per_site * TS * 16 + red;
+}
 
 struct Workspace;  // solver workspace (solver.cu)
 
@@ -253,6 +264,7 @@ struct hisq_ctx {
     hisq::Geom geom;
     int device;
     cudaStream_t stream;
+    int *dev_err = nullptr;  // set by a kernel whose bounded wait ran out (read by hisq_device_status)
     int num_sms;
     hisq_solver_params params;
     std::map<hisq::TuneKey, hisq::LaunchShape> tuned;

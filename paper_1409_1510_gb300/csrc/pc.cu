@@ -575,6 +575,7 @@ int hisq_pc_create(hisq_pc **out, const double *weights) {
     }
     pc->ctx = ctx;
     pc->form = HISQ_PC_NORMAL;
+    pc->train_steps = 0;
     pc->work = new PcState();
     bool ok = cudaMalloc(&pc->d_weights, sizeof(float2) * HISQ_PC_WEIGHTS) == cudaSuccess &&
               cudaMalloc(&pc->d_theta, sizeof(pc->weights)) == cudaSuccess &&
@@ -615,6 +616,7 @@ int hisq_pc_set_weights(hisq_pc *pc, const double *weights) {
     memcpy(pc->weights, weights, sizeof(pc->weights));
     cudaMemsetAsync(pc->d_m, 0, sizeof(pc->weights), ctx->stream);
     cudaMemsetAsync(pc->d_v, 0, sizeof(pc->weights), ctx->stream);
+    pc->train_steps = 0;  // new weights start a new Adam run
     return upload_weights(pc, ctx->stream);
 }
 
@@ -757,7 +759,7 @@ int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, do
         return set_error(HISQ_ERR_NOMEM, "training minibatch allocation failed");
     }
     int rc = HISQ_OK;
-    int step = 0;
+    int step = pc->train_steps;  // a later call continues the same Adam run
     for (int ep = 0; ep < epochs && rc == HISQ_OK; ep++) {
         double loss_sum = 0.0;
         int nb = 0;
@@ -801,6 +803,7 @@ int hisq_pc_train(hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, do
     cudaStreamSynchronize(st);
     cudaFree(rb);
     cudaFree(eb);
+    pc->train_steps = step;
     if (rc == HISQ_OK) {
         HISQ_CUDA(cudaMemcpy(pc->weights, pc->d_theta, sizeof(pc->weights), cudaMemcpyDeviceToHost));
     }

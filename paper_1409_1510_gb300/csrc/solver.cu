@@ -342,6 +342,7 @@ struct Workspace {
     int prec = -1;
     void *b_hi = nullptr, *x_hi = nullptr, *x_lo = nullptr, *r_lo = nullptr, *p = nullptr, *Ap = nullptr;
     void *t = nullptr, *t64 = nullptr, *z = nullptr, *r_old = nullptr;
+    void *q = nullptr, *rp = nullptr;  // single-reduction CG: q = A p and r in the storage precision
     double *canon = nullptr;      // canonical FP64 staging [cap_n][Vh][6]
     SolverState *st = nullptr;    // device
     SolverState *h_st = nullptr;  // pinned host mirror
@@ -365,10 +366,10 @@ void free_graph(GraphCache &gc) {
 }
 
 static void free_buffers(Workspace *w) {
-    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->canon};
+    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->q, w->rp, w->canon};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = nullptr;
+    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = w->q = w->rp = nullptr;
     w->canon = nullptr;
     w->cap_n = 0;
     w->prec = -1;
@@ -408,6 +409,7 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
         {&w->x_lo, vector_bytes(Q, Vh, cap)},         {&w->r_lo, vector_bytes(Q, Vh, cap)},
         {&w->p, vector_bytes(prec, Vh, cap)},         {&w->Ap, vector_bytes(prec, Vh, cap)},
         {&w->t, vector_bytes(prec, Vh, cap)},         {&w->t64, vector_bytes(HISQ_FP64, Vh, cap)},
+        {&w->q, vector_bytes(prec, Vh, cap)},         {&w->rp, vector_bytes(prec, Vh, cap)},
         {(void **)&w->canon, (size_t)cap * Vh * 6 * sizeof(double)},
     };
     for (auto &a : allocs)
@@ -636,7 +638,8 @@ static int enqueue_setup(const Solve &S) {
     return blas(S, HOOK_INIT);
 }
 
-static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol) {
+static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol,
+                            bool cg1 = false) {
     const hisq_solver_params &P = S.ctx->params;
     SolverState *h = S.w->h_st;
     memset(h, 0, sizeof(SolverState));
@@ -652,6 +655,7 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->h_upd = h_upd;
     h->cond_loop = 1;  // the defaults the graph assigns at launch
     h->cond_upd = 0;
+    h->cg1 = cg1 ? 1 : 0;
     HISQ_CUDA(cudaMemcpyAsync(S.w->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, S.st));
     return HISQ_OK;
 }
@@ -747,22 +751,22 @@ static int build_graph(const Solve &S) {
 // ------------------------------------------------------------------------------------------
 // Persistent driver: the whole plain-CG solve of a bundle in one cooperative launch
 // ------------------------------------------------------------------------------------------
-static cudaError_t persistent_occ(int prec, int R, int threads, size_t smem, int *per_sm) {
+static cudaError_t persistent_occ(int prec, int R, bool cg1, int threads, size_t smem, int *per_sm) {
     switch (prec) {
-    case HISQ_FP64: return persistent_occupancy<HISQ_FP64>(R, threads, smem, per_sm);
-    case HISQ_FP32: return persistent_occupancy<HISQ_FP32>(R, threads, smem, per_sm);
-    case HISQ_FP16: return persistent_occupancy<HISQ_FP16>(R, threads, smem, per_sm);
-    default: return persistent_occupancy<HISQ_BF16>(R, threads, smem, per_sm);
+    case HISQ_FP64: return persistent_occupancy<HISQ_FP64>(R, cg1, threads, smem, per_sm);
+    case HISQ_FP32: return persistent_occupancy<HISQ_FP32>(R, cg1, threads, smem, per_sm);
+    case HISQ_FP16: return persistent_occupancy<HISQ_FP16>(R, cg1, threads, smem, per_sm);
+    default: return persistent_occupancy<HISQ_BF16>(R, cg1, threads, smem, per_sm);
     }
 }
 
-static cudaError_t persistent_launch(int prec, const PersArgs &a, int R, int grid, int threads, size_t smem,
+static cudaError_t persistent_launch(int prec, const PersArgs &a, int R, bool cg1, int grid, int threads, size_t smem,
                                      cudaStream_t st) {
     switch (prec) {
-    case HISQ_FP64: return launch_persistent_prec<HISQ_FP64>(a, R, grid, threads, smem, st);
-    case HISQ_FP32: return launch_persistent_prec<HISQ_FP32>(a, R, grid, threads, smem, st);
-    case HISQ_FP16: return launch_persistent_prec<HISQ_FP16>(a, R, grid, threads, smem, st);
-    default: return launch_persistent_prec<HISQ_BF16>(a, R, grid, threads, smem, st);
+    case HISQ_FP64: return launch_persistent_prec<HISQ_FP64>(a, R, cg1, grid, threads, smem, st);
+    case HISQ_FP32: return launch_persistent_prec<HISQ_FP32>(a, R, cg1, grid, threads, smem, st);
+    case HISQ_FP16: return launch_persistent_prec<HISQ_FP16>(a, R, cg1, grid, threads, smem, st);
+    default: return launch_persistent_prec<HISQ_BF16>(a, R, cg1, grid, threads, smem, st);
     }
 }
 
@@ -780,9 +784,12 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     int threads = std::min(pers_threads(R), PERS_DEFAULT_THREADS);
     const int want = S.ctx->params.persistent_threads;
     if (want >= 32 && want <= pers_threads(R) && want % 32 == 0) threads = want;
-    const size_t smem = (size_t)(threads * R + 64) * sizeof(double);
+    const size_t smem = (size_t)(2 * threads * R + 64) * sizeof(double);  // two dot sets (single reduction)
     int per_sm = 0;
-    if (persistent_occ(S.prec, R, threads, smem, &per_sm) != cudaSuccess || per_sm < 1) {
+    // single-reduction CG needs <p, A p> = <r, A r> - beta <r, r> / alpha_prev to survive rounding;
+    // BF16's 8-bit mantissa does not keep it, so BF16 storage iterates in Hestenes-Stiefel form
+    const bool cg1 = S.ctx->params.single_reduction != 0 && S.prec != HISQ_BF16;
+    if (persistent_occ(S.prec, R, cg1, threads, smem, &per_sm) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return HISQ_OK;
     }
@@ -802,6 +809,8 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     a.p = w->p;
     a.t = w->t;
     a.ap = w->Ap;
+    a.q = w->q;
+    a.rp = w->rp;
     a.x = w->x_lo;
     a.r = w->r_lo;
     a.b = w->b_hi;
@@ -819,7 +828,7 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
         a.expected = grid + 1;
         a.spin_limit = 1LL << 12;
     }
-    HISQ_CHECK(set_state_params(S, 0, 0, tol));
+    HISQ_CHECK(set_state_params(S, 0, 0, tol, cg1));
     HISQ_CHECK(pack_vectors(S.ctx, w->canon, w->b_hi, S.n, HISQ_FP64, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->bar, 0, sizeof(unsigned int) * 4, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int) * 4, S.st));
@@ -828,7 +837,7 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
         HISQ_CUDA(cudaMemsetAsync(w->phase_ns, 0, sizeof(unsigned long long) * 8, S.st));
         HISQ_CUDA(cudaEventRecord(w->ev0, S.st));
     }
-    cudaError_t e = persistent_launch(S.prec, a, R, grid, threads, smem, S.st);
+    cudaError_t e = persistent_launch(S.prec, a, R, cg1, grid, threads, smem, S.st);
     if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
         cudaGetLastError();
         return HISQ_OK;  // not co-resident here: the graph driver takes the bundle

@@ -69,13 +69,23 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     const int Ts[] = {256, 128, 64, 32};
     int rc = HISQ_OK;
     const int recon = use64 ? 18 : naik->recon;
+    const int words = link_words(prec, 18) + link_words(prec, recon);
     for (int R : Rs) {
         if (n % R != 0) continue;
         if (prec == HISQ_FP64 && R > 4) continue;
-        for (int S = 1; S <= 4; S *= 2) {
-        if (S > 1 && (recon != 18 || R > 8 / S)) continue;
+        for (int S = 1; S <= 8; S *= 2) {
+        if (S > 1 && (recon != 18 || R > 8 / std::min(S, 4))) continue;
+        if (S == 8 && (prec == HISQ_FP64 || R > 2)) continue;
         for (int T : Ts) {
             LaunchShape sh{R, T, S};
+            if (S == 8) {
+                // staged: sites per tile 32 T / 256 (32..256) times 4 t lanes, within one block
+                const int t = n / R, TS = T / 2;
+                sh.threads = 4 * t * TS;
+                if (sh.threads > 512 || sh.threads % 32 ||
+                    staged_smem(words, TS, sh.threads, n, false) > 200 * 1024)
+                    continue;
+            }
             float ms = 0;
             rc = time_shape(ctx, fat, naik, use64, n, sh, in, out, flush, flush_bytes, &ms);
             if (rc != HISQ_OK) break;
@@ -194,12 +204,21 @@ extern "C" int hisq_set_launch_shape(int prec, int recon, int nrhs, int rhs_per_
     int R = rhs_per_thread;
     if ((R != 1 && R != 2 && R != 4 && R != 8) || nrhs % R != 0 || (prec == HISQ_FP64 && R > 4))
         return set_error(HISQ_ERR_ARG, "rhs_per_thread %d is not available for nrhs %d", R, nrhs);
-    if (block_threads < 32 || block_threads > 256) return set_error(HISQ_ERR_ARG, "block_threads must be in 32..256");
+    if (block_threads < 32 || block_threads > (lanes_per_site == 8 ? 512 : 256))
+        return set_error(HISQ_ERR_ARG, "block_threads must be in 32..256 (32..512 staged)");
     if (lanes_per_site != 1 && !(lanes_per_site == 2 && recon == 18 && R <= 4) &&
-        !(lanes_per_site == 4 && recon == 18 && R <= 2))
+        !(lanes_per_site == 4 && recon == 18 && R <= 2) &&
+        !(lanes_per_site == 8 && recon == 18 && R <= 2 && prec != HISQ_FP64))
         return set_error(HISQ_ERR_ARG,
-                         "lanes_per_site must be 1, 2 (18-real Naik links, rhs_per_thread <= 4) or 4 (18-real Naik "
-                         "links, rhs_per_thread <= 2)");
+                         "lanes_per_site must be 1, 2 (18-real Naik links, rhs_per_thread <= 4), 4 (18-real Naik "
+                         "links, rhs_per_thread <= 2) or 8 (as 4, with staged link records; not FP64)");
+    if (lanes_per_site == 8) {
+        const int t = nrhs / R, words = link_words(prec, 18) + link_words(prec, recon);
+        if (block_threads % (4 * t) || block_threads % 32 || block_threads > 512 ||
+            staged_smem(words, block_threads / (4 * t), block_threads, nrhs, true) > 227 * 1024)
+            return set_error(HISQ_ERR_ARG, "staged shape: block_threads must be a multiple of 4 * nrhs / "
+                                           "rhs_per_thread and of 32, at most 512, within shared memory");
+    }
     ctx->tuned[TuneKey{prec, recon, nrhs, 0}] = LaunchShape{R, block_threads, lanes_per_site};
     ctx->tune_generation++;
     return HISQ_OK;

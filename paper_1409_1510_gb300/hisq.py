@@ -32,7 +32,8 @@ class hisq_solver_params(ctypes.Structure):
                 ("bundle", ctypes.c_int), ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("pc", ctypes.c_void_p), ("stall_window", ctypes.c_int), ("stall_factor", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int),
-                ("debug_barrier_timeout", ctypes.c_int), ("persistent_threads", ctypes.c_int)]
+                ("debug_barrier_timeout", ctypes.c_int), ("persistent_threads", ctypes.c_int),
+                ("single_reduction", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -81,6 +82,7 @@ _SIGNATURES = {
     "hisq_pc_set_weights": ([_VP, _VP], _I),
     "hisq_pc_get_weights": ([_VP, _VP], _I),
     "hisq_pc_apply": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
+    "hisq_device_status": ([], _I),
     "hisq_pc_apply_hermitian": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_apply_adjoint": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_apply_normal": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
@@ -291,3 +293,7 @@ def hisq_pc_train(pc, fat, naik, mass: float, r, e, K: int, batch: int, epochs: 
                   loss_history=None):
     _check(load().hisq_pc_train(pc, fat, naik, float(mass), _ptr(r), _ptr(e), int(K), int(batch), int(epochs),
                                 float(lr), _ptr(loss_history)))
+
+
+def hisq_device_status():
+    _check(load().hisq_device_status())

@@ -41,10 +41,10 @@ def test_every_launch_shape(prec):
         for R in (1, 2, 4, 8):
             if prec == 0 and R == 8:
                 continue
-            for S in (1, 2, 4):
-                if S * R > 8:
+            for S in (1, 2, 4, 8):
+                if min(S, 4) * R > 8 or (S == 8 and prec == 0):
                     continue
-                for threads in (32, 96, 256):
+                for threads in ((32, 96, 256) if S < 8 else (32 * (n // R), 64 * (n // R))):
                     g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads, S)
                     vout.zero_()
                     g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, 1)
@@ -54,13 +54,13 @@ def test_every_launch_shape(prec):
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("n", [1, 3])
 def test_lane_split_with_fused_epilogues(prec, n):
-    """The two-lane (fat / Naik) and four-lane (two directions of one kind) splits with the
-    A-operator epilogue and its fused dot."""
+    """The two-lane (fat / Naik) and four-lane (two directions of one kind) splits, and the
+    four-lane split with staged link records, with the A-operator epilogue and its fused dot."""
     mass = 0.2
     with gpu(DIMS, prec, 18) as g:
         v = _rhs(g.lat, n, 80)
-        for S in (1, 2, 4):
-            g.hisq.hisq_set_launch_shape(prec, 18, n, 1, 128, S)
+        for S in ((1, 2, 4) if prec == 0 else (1, 2, 4, 8)):
+            g.hisq.hisq_set_launch_shape(prec, 18, n, 1, 128 if S < 8 else 32 * 4 * n, S)
             vin, vout = g.pack(v), g.bundle(n)
             pap = np.zeros(n)
             g.hisq.hisq_aop(g.fat, g.naik, mass, vin, vout, n, pap)
@@ -154,3 +154,21 @@ def test_launch_shape_validation():
         for bad in ((1, 18, 4, 4, 128, 4), (1, 13, 4, 1, 128, 2), (1, 18, 4, 1, 128, 3)):
             with pytest.raises(HisqError):
                 h.hisq_set_launch_shape(*bad)
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_staged_tiles_cover_ragged_lattice_and_report_no_timeout(prec):
+    """The staged kernel on a lattice whose half volume is not a multiple of its tile (the last
+    tile's bulk copies are shorter), more tiles than blocks (both stages reused), then the
+    device status: no bounded wait ran out."""
+    dims = (6, 10, 6, 8)  # V/2 = 1440: 11 tiles of 128 sites plus 32, 22 of 64 plus 32, 45 of 32
+    with gpu(dims, prec, 18) as g:
+        # FP32 records are twice as large: half the tile for one right-hand side
+        for n, R, threads in ((1, 1, 512 if prec != 1 else 256), (2, 2, 256), (3, 1, 384)):
+            g.hisq.hisq_set_launch_shape(prec, 18, n, R, threads, 8)
+            v = _rhs(g.lat, n, 90)
+            vin, vout = g.pack(v), g.bundle(n)
+            for parity in (0, 1):
+                g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, parity)
+                assert rel_err(g.unpack(vout, n), g.oracle.dslash_eo(v, parity)) <= PREC_TOL[prec], (n, parity)
+        g.hisq.hisq_device_status()
