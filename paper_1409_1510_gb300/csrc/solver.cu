@@ -333,6 +333,7 @@ struct GraphCache {
     const hisq_pc *pc = nullptr;
     int pc_form = -1;
     double mass = 0;
+    unsigned long long h_loop = 0, h_upd = 0;  // the graph's conditional handles
     int n = 0, prec = -1;
     unsigned tune_generation = 0;
 };
@@ -697,8 +698,6 @@ static int build_graph(const Solve &S) {
     C.timing = false;
     // the state parameters (including the handles) are copied before the graph launch, so the
     // graph itself only holds: setup; WHILE(loop) { head; IF(update) { update }; p-update }
-    w->h_st->h_loop = (unsigned long long)h_loop;
-    w->h_st->h_upd = (unsigned long long)h_upd;
     cudaError_t e = cudaStreamBeginCaptureToGraph(cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) rc = set_error(HISQ_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     cudaGraph_t while_body = nullptr;
@@ -737,6 +736,8 @@ static int build_graph(const Solve &S) {
         return rc;
     }
     w->gc.graph = graph;
+    w->gc.h_loop = (unsigned long long)h_loop;
+    w->gc.h_upd = (unsigned long long)h_upd;
     w->gc.fat = S.fat;
     w->gc.naik = S.naik;
     w->gc.mass = S.mass;
@@ -883,18 +884,15 @@ static int solve_bundle(Solve &S, double tol) {
                      w->gc.n == S.n && w->gc.prec == S.prec && w->gc.pc == S.pc &&
                      w->gc.pc_form == (S.pc ? S.pc->form : -1) &&
                      w->gc.tune_generation == S.ctx->tune_generation;
-        unsigned long long hl = w->h_st->h_loop, hu = w->h_st->h_upd;
-        if (!reuse) {
-            HISQ_CHECK(build_graph(S));
-            hl = w->h_st->h_loop;
-            hu = w->h_st->h_upd;
-        }
+        if (!reuse) HISQ_CHECK(build_graph(S));
+        // the handles live with the graph, not in the state mirror (which every driver rewrites):
+        // the device ends the WHILE loop only through them, so a graph never runs without both
+        const unsigned long long hl = w->gc.h_loop, hu = w->gc.h_upd;
+        if (!hl || !hu) return set_error(HISQ_ERR_STATE, "captured solve graph without its conditional handles");
         HISQ_CHECK(set_state_params(S, hl, hu, tol));
         HISQ_CUDA(cudaGraphLaunch(w->gc.exec, S.st));
         HISQ_CUDA(cudaMemcpyAsync(w->h_st, w->st, sizeof(SolverState), cudaMemcpyDeviceToHost, S.st));
         HISQ_CUDA(cudaStreamSynchronize(S.st));
-        w->h_st->h_loop = hl;
-        w->h_st->h_upd = hu;
         return HISQ_OK;
     }
     HISQ_CHECK(set_state_params(S, 0, 0, tol));

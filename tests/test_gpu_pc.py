@@ -294,3 +294,17 @@ def test_set_form_validation():
         pc = g.hisq.hisq_pc_create(None)
         with pytest.raises(HisqError):
             g.hisq.hisq_pc_set_form(pc, 7)
+
+
+def test_flexible_cg_graph_reused_after_a_persistent_plain_solve():
+    """Flexible CG (captured graph), then plain CG (persistent kernel), then flexible CG again in
+    the same context: the reused graph still terminates and converges."""
+    mass = 0.05
+    with gpu(DIMS, 1) as g:
+        pc = g.hisq.hisq_pc_create(None)
+        rhs = [hi.gaussian_rhs(g.lat, 900 + k) for k in range(2)]
+        _, s1, it1 = _fcg(g, pc, rhs, mass, graph=1)
+        _, s2, it2 = _fcg(g, None, rhs, mass, graph=2)
+        x3, s3, it3 = _fcg(g, pc, rhs, mass, graph=1)
+        assert s1.converged == s3.converged == 2 and np.array_equal(it1, it3)
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x3, mass) <= TOL * 1.01)

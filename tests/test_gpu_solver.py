@@ -204,3 +204,19 @@ def test_bundle_size_chosen_by_the_autotuner():
         x, s, _, res = _solve(g, rhs, 0.05, inner_prec=2, bundle=0, autotune=0)
         assert s.bundle_size == 6 and s.bundles == 1 and s.converged == 6
         assert np.all(g.oracle.true_residual(np.stack(rhs), x, 0.05) <= TOL * SLACK)
+
+
+def test_graph_reused_after_persistent_solves():
+    """Alternating drivers in one context: the captured graph is rebuilt once and then reused
+    after persistent-kernel solves have rewritten the host copy of the bundle state (the graph's
+    loop ends only through its own conditional handles, which live with the graph)."""
+    dims = (8, 10, 8, 6)
+    with gpu(dims, 1) as g:
+        b = hi.gaussian_rhs(g.lat, 95)
+        its = []
+        for driver in (1, 2, 1, 2, 1):
+            x, s, iters, res = _solve(g, [b], 0.05, inner_prec=1, use_graph=driver, bundle=1)
+            assert s.converged == 1 and res[0] <= TOL, driver
+            its.append(int(iters[0]))
+        assert its[0] == its[2] == its[4]
+        assert g.oracle.true_residual(b, x[0], 0.05)[0] <= TOL * SLACK
