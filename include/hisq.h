@@ -187,11 +187,11 @@ typedef struct {
     int persistent_threads; /* block size of the persistent solve kernel: 0 = 512; otherwise a
                              multiple of 32 up to 1024 (one right-hand side per thread) or 512;
                              the grid is every block that fits on the GPU at once */
-    int single_reduction; /* persistent driver: 1 (default) single-reduction CG (Chronopoulos &
-                             Gear 1989: |r|^2 and <r, A r> in one reduction, q = A p by recurrence;
-                             three grid barriers an iteration; not with BF16 storage, whose
-                             rounding breaks the recurrence for <p, A p>), 0 Hestenes-Stiefel
-                             (two reductions, four barriers) as in the other drivers */
+    int single_reduction; /* persistent driver: 1 (default) Hestenes-Stiefel CG with one
+                             reduction per iteration (<p, A p>, |A p|^2 and the update phase's
+                             |r|^2 together; beta from |r - alpha A p|^2 = alpha^2 |A p|^2 - |r|^2),
+                             three grid barriers an iteration; 0 the two-reduction form of the
+                             other drivers, four barriers */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);

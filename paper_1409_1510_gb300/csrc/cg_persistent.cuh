@@ -19,8 +19,7 @@ struct PersArgs {
     Geom g;
     LinkField fat, naik;      // inner precision (18-real Naik)
     LinkField fat64, naik64;  // FP64 copies
-    void *p, *t, *ap;         // inner precision bundles (ap: A p, or A r = s in single-reduction CG)
-    void *q, *rp;             // single-reduction CG: q = A p and r in the storage precision
+    void *p, *t, *ap;         // inner precision bundles
     void *x, *r;              // x_lo and r in the iterated precision
     void *b, *xhi, *t64;      // FP64
     double mass2;
@@ -74,7 +73,7 @@ __device__ __forceinline__ void clock_store(const PhaseClock &c, unsigned long l
         for (int i = 0; i < PERS_PHASES; i++) out[i] = c.acc[i];
 }
 
-constexpr int PERS_ND = 2 * HISQ_MAX_BUNDLE;
+constexpr int PERS_ND = 3 * HISQ_MAX_BUNDLE;  // up to three dots per right-hand side
 
 __device__ __forceinline__ bool grid_sync(const PersArgs &a) {
     __shared__ int s_ok;
@@ -166,23 +165,25 @@ __device__ __forceinline__ void publish_dots(const PersArgs &a, double *red, dou
     }
 }
 
-// The same for two sets of dots in one pass: dot[k][r] is column k n + gi R + r (n = t R); red
-// holds 2 blockDim.x * R doubles.
-template <int R>
-__device__ __forceinline__ void publish_dots2(const PersArgs &a, double *red, double (&dot)[2][R], int t, int gi,
-                                              int n) {
+// The same for K sets of dots in one pass: dot[k][r] is column k step + gi R + r (n = t R,
+// step >= n); red holds K blockDim.x * R doubles.
+template <int R, int K>
+__device__ __forceinline__ void publish_dots_k(const PersArgs &a, double *red, double (&dot)[K][R], int t, int gi,
+                                               int n, int step) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int nd = 2 * n;
+    const int nd = K * n;
+    // set k, column j of the set, lands in partials column k * step + j
+    auto column = [&](int jj) { return (jj / n) * step + jj % n; };
     __syncthreads();  // red may still be read by the previous step
     if ((t & (t - 1)) == 0 && t <= 32) {
         for (int off = 16; off >= t; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < 2; k++)
+            for (int k = 0; k < K; k++)
 #pragma unroll
                 for (int r = 0; r < R; r++) dot[k][r] += __shfl_xor_sync(0xffffffffu, dot[k][r], off);
         if (lane < t) {
 #pragma unroll
-            for (int k = 0; k < 2; k++)
+            for (int k = 0; k < K; k++)
 #pragma unroll
                 for (int r = 0; r < R; r++)
                     if (gi * R + r < n) red[warp * nd + k * n + gi * R + r] = dot[k][r];
@@ -192,7 +193,7 @@ __device__ __forceinline__ void publish_dots2(const PersArgs &a, double *red, do
             double s = lane < nwarps ? red[lane * nd + j] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+            if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + column(j)] = s;
         }
         return;
     }
@@ -201,7 +202,7 @@ __device__ __forceinline__ void publish_dots2(const PersArgs &a, double *red, do
     __syncthreads();
     if (row < rows) {
 #pragma unroll
-        for (int k = 0; k < 2; k++)
+        for (int k = 0; k < K; k++)
 #pragma unroll
             for (int r = 0; r < R; r++)
                 if (gi * R + r < n) red[row * nd + k * n + gi * R + r] = dot[k][r];
@@ -212,7 +213,7 @@ __device__ __forceinline__ void publish_dots2(const PersArgs &a, double *red, do
         for (int q = lane; q < rows; q += 32) s += red[q * nd + j];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + j] = s;
+        if (lane == 0) a.partials[(size_t)blockIdx.x * PERS_ND + column(j)] = s;
     }
 }
 
@@ -245,14 +246,14 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
 
 // One Dslash phase over the block's share of the sites of output parity `parity`, input from the
 // loader `in`.  EPI_PLAIN: out = D in.  EPI_AOP: out = m^2 ax - D in with Re<ax, out> per block
-// (ax from the loader `ax` at the output site); with DOTS2 also |ax|^2, published as the first n
-// columns (Re<ax, out> then follows as columns n..2n-1).  EPI_RESID (FP64): r = b - m^2 ax + D in,
-// written to out_lo (iterated precision Q), and to out_p (storage precision P) if given, with
-// |r|^2 per block.  mask[r] selects right-hand sides.
-template <int PP, int R, int EPI, int Q, class IN, class AX, bool DOTS2 = false, int P = PP>
+// (ax from the loader `ax` at the output site); with DOTS2 also |out|^2, published as columns
+// 2n..3n-1 (columns n..2n-1 are left to the update phase's |r|^2).  EPI_RESID (FP64):
+// r = b - m^2 ax + D in, written to out_lo (iterated precision Q) with |r|^2 per block.  mask[r]
+// selects right-hand sides.
+template <int PP, int R, int EPI, int Q, class IN, class AX, bool DOTS2 = false>
 __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
                                              const IN &in, void *out, int parity, const int *mask, const AX &ax,
-                                             const void *bvec, void *out_lo, double *red, void *out_p = nullptr) {
+                                             const void *bvec, void *out_lo, double *red) {
     using real = typename Prec<PP>::real;
     const Geom &g = a.g;
     const int n = a.n, t = n / R, spb = blockDim.x / t;
@@ -265,9 +266,11 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
         act[r] = r0 + r < n && mask[r0 + r] != 0;
         any |= act[r];
     }
-    double dot[R], dot2[R];  // Re<ax, out>; |ax|^2 (DOTS2)
+    double dot[2][R];  // Re<ax, out>; with DOTS2 also |out|^2
 #pragma unroll
-    for (int r = 0; r < R; r++) dot[r] = dot2[r] = 0.0;
+    for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int r = 0; r < R; r++) dot[k][r] = 0.0;
     const int ts = tile_sites(g.Vh, spb);
     if (any && sl < ts) {
         for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
@@ -287,16 +290,20 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                 for (int r = 0; r < R; r++) {
                     if (!act[r]) continue;
                     Cplx<real> w[3];
-                    real d = 0, d2 = 0;
+                    real d = 0;
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
                         w[c] = {m2 * p[r][c].re - acc[r][c].re, m2 * p[r][c].im - acc[r][c].im};
                         d += p[r][c].re * w[c].re + p[r][c].im * w[c].im;
-                        if constexpr (DOTS2) d2 += p[r][c].re * p[r][c].re + p[r][c].im * p[r][c].im;
                     }
-                    dot[r] += (double)d;
-                    if constexpr (DOTS2) dot2[r] += (double)d2;
+                    dot[0][r] += (double)d;
                     store_vec<PP>(vout, s, r0 + r, w);
+                    if constexpr (DOTS2) {
+                        real f = 0;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) f += w[c].re * w[c].re + w[c].im * w[c].im;
+                        dot[1][r] += (double)f;
+                    }
                 }
             } else {
                 static_assert(EPI == EPI_RESID && PP == HISQ_FP64, "residual epilogue is FP64");
@@ -318,29 +325,16 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                         d += wr * wr + wi * wi;
                         lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
                     }
-                    dot[r] += d;
+                    dot[0][r] += d;
                     store_vec<Q>(vlo, s, r0 + r, lo3);
-                    if (out_p) {
-                        Cplx<typename Prec<P>::real> lp[3];
-#pragma unroll
-                        for (int c = 0; c < 3; c++)
-                            lp[c] = {(typename Prec<P>::real)lo3[c].re, (typename Prec<P>::real)lo3[c].im};
-                        store_vec<P>(VecView<P>{out_p, n}, s, r0 + r, lp);
-                    }
                 }
             }
         }
     }
     if constexpr (DOTS2) {
-        double both[2][R];
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            both[0][r] = dot2[r];
-            both[1][r] = dot[r];
-        }
-        publish_dots2<R>(a, red, both, t, gi, n);
+        publish_dots_k<R, 2>(a, red, dot, t, gi, n, 2 * n);
     } else if constexpr (EPI != EPI_PLAIN) {
-        publish_dots<R>(a, red, dot, t, gi, n);
+        publish_dots<R>(a, red, dot[0], t, gi, n);
     }
 }
 

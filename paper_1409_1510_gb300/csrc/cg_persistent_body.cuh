@@ -53,17 +53,7 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
                 store_vec<HISQ_FP64>(V64(xhi), s, r, z64);
                 store_vec<Q>(VQ(x), s, r, zq);
                 store_vec<Q>(VQ(r), s, r, bq);
-                if constexpr (CG1) {  // p_{-1} = q_{-1} = 0 and r in the storage precision
-                    const Cplx<rp> zp[3] = {{0, 0}, {0, 0}, {0, 0}};
-                    Cplx<rp> bqp[3];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) bqp[c] = {(rp)bq[c].re, (rp)bq[c].im};
-                    store_vec<P>(VP(p), s, r, zp);
-                    store_vec<P>(VP(q), s, r, zp);
-                    store_vec<P>(VP(rp), s, r, bqp);
-                } else {
-                    store_vec<P>(VP(p), s, r, bp);
-                }
+                store_vec<P>(VP(p), s, r, bp);
             }
         }
         publish_dots<1>(a, red, acc, n, r, n);
@@ -76,86 +66,97 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
     }
     clock_start(clk, a.phase_ns);
 
-    // ---- single-reduction CG (Chronopoulos & Gear): three phases and one reduction an iteration ----
+    // ---- Hestenes-Stiefel CG with one reduction: three phases an iteration ----
     while (CG1 && ok && st.any_active && st.bundle_iters < st.max_iter) {
-        // t = D_oe r
-        dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(rp)}, a.t, 1, st.active,
-                                         PlainIn<P, true>{VP(rp)}, nullptr, nullptr, red);
+        // t = D_oe p
+        dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(p)}, a.t, 1, st.active,
+                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_DOE);
-        // s = A r = m^2 r - D_eo t with |r|^2 and <r, A r>
+        // A p = m^2 p - D_eo t with <p, A p> and |A p|^2 (|r|^2 came from the previous update phase)
         dslash_phase<P, R, EPI_AOP, Q, PlainIn<P, true>, PlainIn<P, true>, true>(
-            a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active, PlainIn<P, true>{VP(rp)}, nullptr, nullptr,
+            a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active, PlainIn<P, true>{VP(p)}, nullptr, nullptr,
             red);
         if (!(ok = grid_sync(a))) break;
-        sum_partials(a, red, 2 * n, dots);
+        sum_partials(a, red, 3 * n, dots);
         if (tid == 0) run_hook(HOOK_CG1, &st, dots, n);
         __syncthreads();
         clock_mark(clk, PH_AOP);
-        // p = r + beta p; q = s + beta q (= A p); x += alpha p; r -= alpha q; r in the storage
-        // precision for the next Dslash; then, if due, x_hi += x and x = 0 (same sites, same thread)
+        // x += alpha p; r -= alpha A p with |r|^2 (for the next iteration's step); p = r + beta p,
+        // except where an FP64 recomputation is due (there x_hi += x, x = 0, and p waits for the
+        // true residual)
+        double rr_acc[1] = {0.0};
         if (st.active[r] && row_ok) {
             const rq al = (rq)st.alpha[r][0];
             const rp be = (rp)st.beta[r][0];
-            const bool fold = st.update[r] != 0;
+            const bool upd = st.update[r] != 0;
             for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
                 const int s = tile * ts + sl;
                 if (s >= a.g.Vh) break;
-                Cplx<rp> rl[3], sv[3], p[3], q[3];
+                Cplx<rp> p[3], ap[3];
                 Cplx<rq> x[3], rv[3];
-                load_vec<P, true>(VP(rp), s, r, rl);
-                load_vec<P, true>(VP(ap), s, r, sv);
                 load_vec<P, true>(VP(p), s, r, p);
-                load_vec<P, true>(VP(q), s, r, q);
+                load_vec<P, true>(VP(ap), s, r, ap);
                 load_vec<Q, true>(VQ(x), s, r, x);
                 load_vec<Q, true>(VQ(r), s, r, rv);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    p[c] = {rl[c].re + be * p[c].re, rl[c].im + be * p[c].im};
-                    q[c] = {sv[c].re + be * q[c].re, sv[c].im + be * q[c].im};
                     x[c].re += al * (rq)p[c].re;
                     x[c].im += al * (rq)p[c].im;
-                    rv[c].re -= al * (rq)q[c].re;
-                    rv[c].im -= al * (rq)q[c].im;
-                    rl[c] = {(rp)rv[c].re, (rp)rv[c].im};
+                    rv[c].re -= al * (rq)ap[c].re;
+                    rv[c].im -= al * (rq)ap[c].im;
                 }
-                store_vec<P>(VP(p), s, r, p);
-                store_vec<P>(VP(q), s, r, q);
                 store_vec<Q>(VQ(r), s, r, rv);
-                store_vec<P>(VP(rp), s, r, rl);
-                store_vec<Q>(VQ(x), s, r, x);
-            }
-            if (fold) {  // the same sites and thread: x was just written by this thread
-                for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
-                    const int s = tile * ts + sl;
-                    if (s >= a.g.Vh) break;
-                    Cplx<rq> x[3];
+                rq part = 0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) part += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+                rr_acc[0] += (double)part;
+                if (upd) {
                     Cplx<double> xh[3];
                     const Cplx<rq> zq[3] = {{0, 0}, {0, 0}, {0, 0}};
-                    load_vec<Q, true>(VQ(x), s, r, x);
                     load_vec<HISQ_FP64, true>(V64(xhi), s, r, xh);
 #pragma unroll
                     for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
                     store_vec<HISQ_FP64>(V64(xhi), s, r, xh);
                     store_vec<Q>(VQ(x), s, r, zq);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
+                    store_vec<Q>(VQ(x), s, r, x);
+                    store_vec<P>(VP(p), s, r, p);
                 }
             }
         }
+        publish_dots<1>(a, red, rr_acc, n, r, n, n);  // partials columns n..2n-1
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_UPDATE);
         if (st.any_update) {
-            // r = b - A x_hi in FP64 (written to r and to its storage-precision copy), |r|^2
+            // r = b - A x_hi in FP64 (written to r), |r|^2; then p = r + beta p with beta from it
             dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
                                                      st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr,
                                                      red);
             if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q, PlainIn<HISQ_FP64, true>, PlainIn<HISQ_FP64, true>, false, P>(
-                a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr, 0, st.update,
-                PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red, a.rp);
+            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
+                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red);
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, n, dots);
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
             __syncthreads();
+            if (st.update[r] && st.active[r] && row_ok) {
+                const rp be = (rp)st.beta[r][0];
+                for (int tile = blockIdx.x; (long)tile * ts < a.g.Vh; tile += gridDim.x) {
+                    const int s = tile * ts + sl;
+                    if (s >= a.g.Vh) break;
+                    Cplx<rq> rv[3];
+                    Cplx<rp> p[3];
+                    load_vec<Q, true>(VQ(r), s, r, rv);
+                    load_vec<P, true>(VP(p), s, r, p);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
+                    store_vec<P>(VP(p), s, r, p);
+                }
+            }
+            if (!(ok = grid_sync(a))) break;
             clock_mark(clk, PH_RELIABLE);
         }
     }
@@ -292,13 +293,19 @@ cudaError_t launch_persistent_prec(const PersArgs &a, int R, bool cg1, int grid,
                                    cudaStream_t st) {
     void *args[] = {const_cast<PersArgs *>(&a)};
     if (P == HISQ_FP64 && R > 2) return cudaErrorInvalidValue;
-    return cudaLaunchCooperativeKernel(persistent_kernel_ptr<P>(R, cg1), grid, threads, args, smem, st);
+    const void *k = persistent_kernel_ptr<P>(R, cg1);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, grid, threads, args, smem, st);
 }
 
 template <int P>
 cudaError_t persistent_occupancy(int R, bool cg1, int threads, size_t smem, int *blocks_per_sm) {
     if (P == HISQ_FP64 && R > 2) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel_ptr<P>(R, cg1), threads, smem);
+    const void *k = persistent_kernel_ptr<P>(R, cg1);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 
 }  // namespace hisq

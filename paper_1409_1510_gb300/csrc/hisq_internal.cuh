@@ -150,6 +150,32 @@ __device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cpl
     }
 }
 
+// The values a colour vector has after store_vec then load_vec (the storage precision's
+// rounding, the FP16 record's shared scale included), computed in registers.
+template <int P>
+__device__ __forceinline__ void round_trip(const Cplx<typename Prec<P>::real> w[3], Cplx<typename Prec<P>::real> out[3]) {
+    if constexpr (P == HISQ_FP64 || P == HISQ_FP32) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) out[c] = w[c];
+    } else if constexpr (P == HISQ_FP16) {
+        float m = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) m = fmaxf(m, fmaxf(fabsf(w[c].re), fabsf(w[c].im)));
+        const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float2 f = __half22float2(__floats2half2_rn(w[c].re * inv, w[c].im * inv));
+            out[c] = {f.x * m, f.y * m};
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float2 f = __bfloat1622float2(__floats2bfloat162_rn(w[c].re, w[c].im));
+            out[c] = {f.x, f.y};
+        }
+    }
+}
+
 template <int P>
 __device__ __forceinline__ void store_vec(const VecView<P> &v, long s, int r, const Cplx<typename Prec<P>::real> w[3]) {
     if constexpr (P == HISQ_FP64) {

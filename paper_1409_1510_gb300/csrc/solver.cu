@@ -343,7 +343,6 @@ struct Workspace {
     int prec = -1;
     void *b_hi = nullptr, *x_hi = nullptr, *x_lo = nullptr, *r_lo = nullptr, *p = nullptr, *Ap = nullptr;
     void *t = nullptr, *t64 = nullptr, *z = nullptr, *r_old = nullptr;
-    void *q = nullptr, *rp = nullptr;  // single-reduction CG: q = A p and r in the storage precision
     double *canon = nullptr;      // canonical FP64 staging [cap_n][Vh][6]
     SolverState *st = nullptr;    // device
     SolverState *h_st = nullptr;  // pinned host mirror
@@ -367,10 +366,10 @@ void free_graph(GraphCache &gc) {
 }
 
 static void free_buffers(Workspace *w) {
-    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->q, w->rp, w->canon};
+    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->canon};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = w->q = w->rp = nullptr;
+    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = nullptr;
     w->canon = nullptr;
     w->cap_n = 0;
     w->prec = -1;
@@ -410,7 +409,6 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
         {&w->x_lo, vector_bytes(Q, Vh, cap)},         {&w->r_lo, vector_bytes(Q, Vh, cap)},
         {&w->p, vector_bytes(prec, Vh, cap)},         {&w->Ap, vector_bytes(prec, Vh, cap)},
         {&w->t, vector_bytes(prec, Vh, cap)},         {&w->t64, vector_bytes(HISQ_FP64, Vh, cap)},
-        {&w->q, vector_bytes(prec, Vh, cap)},         {&w->rp, vector_bytes(prec, Vh, cap)},
         {(void **)&w->canon, (size_t)cap * Vh * 6 * sizeof(double)},
     };
     for (auto &a : allocs)
@@ -639,8 +637,7 @@ static int enqueue_setup(const Solve &S) {
     return blas(S, HOOK_INIT);
 }
 
-static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol,
-                            bool cg1 = false) {
+static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol) {
     const hisq_solver_params &P = S.ctx->params;
     SolverState *h = S.w->h_st;
     memset(h, 0, sizeof(SolverState));
@@ -656,7 +653,6 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->h_upd = h_upd;
     h->cond_loop = 1;  // the defaults the graph assigns at launch
     h->cond_upd = 0;
-    h->cg1 = cg1 ? 1 : 0;
     HISQ_CUDA(cudaMemcpyAsync(S.w->st, h, sizeof(SolverState), cudaMemcpyHostToDevice, S.st));
     return HISQ_OK;
 }
@@ -785,11 +781,9 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     int threads = std::min(pers_threads(R), PERS_DEFAULT_THREADS);
     const int want = S.ctx->params.persistent_threads;
     if (want >= 32 && want <= pers_threads(R) && want % 32 == 0) threads = want;
-    const size_t smem = (size_t)(2 * threads * R + 64) * sizeof(double);  // two dot sets (single reduction)
+    const size_t smem = (size_t)(4 * threads * R + 64) * sizeof(double);  // four dot sets (single reduction)
     int per_sm = 0;
-    // single-reduction CG needs <p, A p> = <r, A r> - beta <r, r> / alpha_prev to survive rounding;
-    // BF16's 8-bit mantissa does not keep it, so BF16 storage iterates in Hestenes-Stiefel form
-    const bool cg1 = S.ctx->params.single_reduction != 0 && S.prec != HISQ_BF16;
+    const bool cg1 = S.ctx->params.single_reduction != 0;
     if (persistent_occ(S.prec, R, cg1, threads, smem, &per_sm) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return HISQ_OK;
@@ -810,8 +804,6 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     a.p = w->p;
     a.t = w->t;
     a.ap = w->Ap;
-    a.q = w->q;
-    a.rp = w->rp;
     a.x = w->x_lo;
     a.r = w->r_lo;
     a.b = w->b_hi;
@@ -829,7 +821,7 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
         a.expected = grid + 1;
         a.spin_limit = 1LL << 12;
     }
-    HISQ_CHECK(set_state_params(S, 0, 0, tol, cg1));
+    HISQ_CHECK(set_state_params(S, 0, 0, tol));
     HISQ_CHECK(pack_vectors(S.ctx, w->canon, w->b_hi, S.n, HISQ_FP64, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->bar, 0, sizeof(unsigned int) * 4, S.st));
     HISQ_CUDA(cudaMemsetAsync(w->err, 0, sizeof(int) * 4, S.st));

@@ -17,7 +17,7 @@ enum Hook {
     HOOK_FCG_ALPHA = 6, // dots = <p, A p>; with <p, r> from HOOK_FCG_PR: alpha for flexible CG
     HOOK_FCG_BETA = 7,  // dots = <r - r_old, z> (complex): beta for flexible CG
     HOOK_FCG_PR = 8,    // dots = <p, r> (complex) of the new direction
-    HOOK_CG1 = 9,       // dots = |r|^2 (n), then Re<r, A r> (n): one-reduction CG step
+    HOOK_CG1 = 9,       // dots = <p, A p>, |r|^2, |A p|^2 (n each): one-reduction CG step
 };
 
 struct SolverState {
@@ -56,7 +56,7 @@ struct SolverState {
     unsigned long long h_upd;
     int cond_loop;                    // last value given to each handle (the graph assigns the
     int cond_upd;                     // defaults 1 and 0 at every launch)
-    int cg1;                          // 1: single-reduction CG (HOOK_CG1 drives the iteration)
+    int pad_;
 };
 static_assert(sizeof(SolverState) % sizeof(uint32_t) == 0, "the state is copied as 32-bit words");
 
@@ -170,44 +170,38 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
         break;
     }
     case HOOK_CG1: {
-        // Chronopoulos & Gear (1989): with gamma = |r_k|^2 and delta = <r_k, A r_k> from one
-        // reduction, beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma / alpha_prev)
-        // (= gamma / <p_k, A p_k>); the update phase then forms p = r + beta p, q = A r + beta q
-        // (= A p), x += alpha p, r -= alpha q.  The FP64 recomputation decision is taken on
-        // gamma (the residual of the current iterate) and runs after that update.
+        // Hestenes-Stiefel CG with one reduction per iteration.  The reduction after A p brings
+        // <p, A p> and |A p|^2 together with |r|^2, which the previous update phase published
+        // (or, right after setup or an FP64 recomputation, the exact value kept in rr): then
+        // alpha = |r|^2 / <p, A p> and, since <r, A p> = <p, A p> (A-conjugacy), the next
+        // residual norm |r - alpha A p|^2 = alpha^2 |A p|^2 - |r|^2 gives beta and the
+        // reliable-update decision before the update phase, which then also forms p = r + beta p.
+        // |r|^2 is measured every iteration and A p recomputed, so no rounding accumulates.
         int any = 0;
         for (int k = 0; k < n; k++) {
+            const bool exact = st->restart[k] || st->update[k];  // rr holds the measured |r|^2
+            st->restart[k] = 0;
             st->update[k] = 0;
             if (!st->active[k]) continue;
-            const double g = dots[k], d = dots[n + k];
-            if (!isfinite(g) || !isfinite(d)) {
+            const double pap = dots[k], apap = dots[2 * n + k];
+            const double g = exact ? st->rr[k] : dots[n + k];
+            if (!(pap > 0.0) || !isfinite(pap) || !isfinite(g) || !isfinite(apap)) {
                 st->active[k] = 0;
                 st->status[k] = RHS_BREAKDOWN;
+                st->alpha[k][0] = 0.0;
                 continue;
             }
-            double beta = 0.0;
-            if (st->restart[k]) st->restart[k] = 0;
-            else beta = g / st->rr[k];
-            double den = beta == 0.0 ? d : d - beta * g / st->alpha[k][0];
-            if (!(den > 0.0) || !isfinite(den)) {
-                // <p, A p> from the recurrence lost to rounding (it is a difference): restart the
-                // direction, p = r and q = A r, for which it is <r, A r> itself
-                beta = 0.0;
-                den = d;
-            }
-            if (!(den > 0.0)) {
-                st->active[k] = 0;
-                st->status[k] = RHS_BREAKDOWN;
-                continue;
-            }
-            st->beta[k][0] = beta;
-            st->beta[k][1] = 0.0;
-            st->alpha[k][0] = g / den;
+            const double al = g / pap;
+            double gn = al * al * apap - g;
+            if (!(gn > 0.0)) gn = 0.0;  // cancellation at convergence: the FP64 check decides
+            st->alpha[k][0] = al;
             st->alpha[k][1] = 0.0;
-            st->rr_prev[k] = st->rr[k];
-            st->rr[k] = g;
             st->iters[k] += 1;
-            const double rn = sqrt(g);
+            st->rr_prev[k] = g;
+            st->beta[k][0] = gn / g;
+            st->beta[k][1] = 0.0;
+            st->rr[k] = gn;
+            const double rn = sqrt(gn);
             const bool at_tol = rn <= st->tol * st->bnorm[k];
             const bool drop = (!st->inner_fp64) && rn < st->delta * st->r_upd[k];
             const bool last = st->iters[k] >= st->max_iter;
@@ -301,10 +295,6 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             } else if (st->iters[k] >= st->max_iter) {
                 st->active[k] = 0;
                 st->status[k] = RHS_NOT_CONVERGED;
-            } else if (st->cg1) {
-                // single-reduction CG: the next step measures |r_true|^2 itself and takes
-                // beta = |r_true|^2 / |r_previous|^2 against the gamma kept in rr
-                st->r_upd[k] = rn;
             } else {
                 // restart the iterated residual from the true one; keep the search direction
                 // with beta = |r_true|^2 / |r_previous|^2 (Sleijpen & van der Vorst reliable update)
