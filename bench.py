@@ -321,6 +321,8 @@ def run_ours(args, rank, world, local_rank, dist):
     gms, _ = timed(max(3, min(args.steps, 10)), inner, 1)
     graph_ms = statistics.median(gms)
 
+    fp32_peak, fp64_peak = hisq.hisq_measure_fma_peaks()  # TFLOP/s, FMA chains on every SM
+
     # ---- roofline of the dominant kernel, the persistent solve kernel of the timed region:
     # algorithmic bytes of each launch (setup, iterations, FP64 recomputations) over its
     # CUDA-event duration; phase times from inside the kernel ----
@@ -341,6 +343,7 @@ def run_ours(args, rank, world, local_rank, dist):
                                 enumerate(("dslash_doe", "dslash_aop_dot", "pxr_update", "fp64_reliable"))},
               "dslash_phases_gbs": ds_gbs, "dslash_phases_frac": ds_gbs / hbm_peak if ds_gbs else None,
               "fp64_reliable_gflops": rel_gflops,
+              "fp64_reliable_frac_of_fp64_fma_peak": rel_gflops / (fp64_peak * 1e3) if rel_gflops else None,
               "fp64_reliable_share": ph[3] / k_ms if k_ms > 0 else None,
               "clock": "%globaltimer read by block 0 after each grid barrier"}
     traffic = kernel_traffic(dims, args.inner)
@@ -455,6 +458,8 @@ def run_ours(args, rank, world, local_rank, dist):
             "other_inner_precisions": variants,
             "bundle_of_16": dict(batched, speedup_per_rhs_vs_single=s_rhs / batched["s_per_rhs"]),
             "roofline": roofline, "cpu_baseline": cpu,
+            "alu_peaks": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
+                          "how": "independent FMA chains on every SM, CUDA events (hisq_measure_fma_peaks)"},
             "e2e": {"value": e2e_value, "unit": "GFlop/s", "h2d_bytes_per_step": vbytes, "d2h_bytes_per_step": vbytes},
             "gpu_launches": int(launches_all), "clocks": clk.summary(), "wall_s_timed_region": t_wall,
         }
@@ -478,6 +483,8 @@ def run_sweep(args):
     d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     hbm_peak, _ = peaks()
+    fp32_peak, fp64_peak = hisq.hisq_measure_fma_peaks()
+    print(json.dumps({"fp32_fma_tflops": fp32_peak, "fp64_fma_tflops": fp64_peak}), flush=True)
     rows = []
     for name in ("fp32", "fp16", "bf16", "fp64"):
         prec = PREC[name]
@@ -504,6 +511,8 @@ def run_sweep(args):
             rows.append({"precision": name, "nrhs": n, "us": sec * 1e6,
                          "gflops": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e9,
                          "gbs": byts / sec / 1e9, "frac_hbm": byts / sec / 1e9 / hbm_peak,
+                         "frac_fma_peak": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e12
+                         / (fp64_peak if prec == 0 else fp32_peak),
                          "shape": {"rhs_per_thread": shape[0], "threads": shape[1], "lanes_per_site": shape[2]}})
             print(json.dumps(rows[-1]), flush=True)
         hisq.hisq_links_destroy(fat)

@@ -86,6 +86,12 @@ int hisq_finalize(void);
  * bound, so a lost transfer ends the kernel instead of hanging it. */
 int hisq_device_status(void);
 
+/* Measured dense FMA throughput of the context's device in TFLOP/s (an FMA counted as two
+ * flops): chains of independent FP32 and FP64 fused multiply-adds on every SM, timed with CUDA
+ * events (about 0.1 s).  The denominators of the FP32- and FP64-bound rooflines; the paper has
+ * no counterpart. */
+int hisq_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops);
+
 const char *hisq_strerror(int status);
 const char *hisq_last_error(void);
 
@@ -124,6 +130,13 @@ int hisq_unpack(const void *internal, double *canon, int nrhs, int prec);
  * naik must share the context and the precision.  Allocates nothing. */
 int hisq_dslash(const hisq_links *fat, const hisq_links *naik, const void *in, void *out,
                 int nrhs, int parity);
+
+/* w = D v on the whole lattice, Eq. (3) as printed (both parities): in and out are each two
+ * internal bundles of nrhs vectors back to back, the even-site bundle first, then the odd-site
+ * one (hisq_vector_bytes(prec, nrhs) bytes each); out_even = D_eo in_odd, out_odd = D_oe in_even.
+ * Same requirements as hisq_dslash; allocates nothing. */
+int hisq_dslash_full(const hisq_links *fat, const hisq_links *naik, const void *in, void *out,
+                     int nrhs);
 
 /* A-operator with fused dot product: out = m^2 in - D_eo (D_oe in) on the even sites, and
  * pAp[r] = Re <in_r, out_r> accumulated in FP64.  in, out: device, internal layout in the links'

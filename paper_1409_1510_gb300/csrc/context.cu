@@ -692,6 +692,29 @@ int hisq_dslash(const hisq_links *fat, const hisq_links *naik, const void *in, v
     return launch_dslash(ctx, fat, naik, false, d, nullptr, ctx->stream);
 }
 
+int hisq_dslash_full(const hisq_links *fat, const hisq_links *naik, const void *in, void *out, int nrhs) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    HISQ_CHECK(check_pair(ctx, fat, naik));
+    if (!in || !out) return set_error(HISQ_ERR_ARG, "null vector");
+    if (nrhs < 1 || nrhs > HISQ_MAX_NRHS) return set_error(HISQ_ERR_ARG, "nrhs must be in 1..%d", HISQ_MAX_NRHS);
+    const size_t half = vector_bytes(fat->prec, ctx->geom.Vh, nrhs);
+    const char *ib = static_cast<const char *>(in);
+    char *ob = static_cast<char *>(out);
+    if (ob < ib + 2 * half && ib < ob + 2 * half) return set_error(HISQ_ERR_ARG, "in and out must not overlap");
+    for (int parity = 0; parity < 2; parity++) {  // output parity; the input is the other half
+        DslashArgs d;
+        memset(&d, 0, sizeof(d));
+        d.in = ib + (size_t)(1 - parity) * half;
+        d.out = ob + (size_t)parity * half;
+        d.n = nrhs;
+        d.parity = parity;
+        d.epi = EPI_PLAIN;
+        HISQ_CHECK(launch_dslash(ctx, fat, naik, false, d, nullptr, ctx->stream));
+    }
+    return HISQ_OK;
+}
+
 int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const void *in, void *out, int nrhs,
              double *pAp) {
     hisq_ctx *ctx;

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "hisq_pc_get_weights": ([_VP, _VP], _I),
     "hisq_pc_apply": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_device_status": ([], _I),
+    "hisq_dslash_full": ([_VP, _VP, _VP, _VP, _I], _I),
+    "hisq_measure_fma_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
     "hisq_pc_apply_hermitian": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_apply_adjoint": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
     "hisq_pc_apply_normal": ([_VP, _VP, _VP, _VP, _VP, _I], _I),
@@ -297,3 +299,14 @@ def hisq_pc_train(pc, fat, naik, mass: float, r, e, K: int, batch: int, epochs: 
 
 def hisq_device_status():
     _check(load().hisq_device_status())
+
+
+def hisq_dslash_full(fat, naik, vin, vout, nrhs: int):
+    _check(load().hisq_dslash_full(fat, naik, _ptr(vin), _ptr(vout), int(nrhs)))
+
+
+def hisq_measure_fma_peaks():
+    """(fp32_tflops, fp64_tflops) measured on the context's device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().hisq_measure_fma_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

@@ -172,3 +172,34 @@ def test_staged_tiles_cover_ragged_lattice_and_report_no_timeout(prec):
                 g.hisq.hisq_dslash(g.fat, g.naik, vin, vout, n, parity)
                 assert rel_err(g.unpack(vout, n), g.oracle.dslash_eo(v, parity)) <= PREC_TOL[prec], (n, parity)
         g.hisq.hisq_device_status()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_full_lattice_dslash_matches_eq3(prec):
+    """Eq. (3) as printed, on both parities: the two halves of the output against the oracle's
+    full-lattice Dslash of the same full-lattice input."""
+    n = 2
+    with gpu(DIMS, prec, 18) as g:
+        lat = g.lat
+        rng = np.random.default_rng(31)
+        v = (rng.standard_normal((n, lat.volume, 3)) + 1j * rng.standard_normal((n, lat.volume, 3))) * np.sqrt(0.5)
+        ev, od = lat.eo_sites(0), lat.eo_sites(1)
+        half = g.hisq.hisq_vector_bytes(prec, n)
+        vin = g.torch.empty(2 * half, dtype=g.torch.uint8, device=g.dev)
+        vout = g.torch.empty_like(vin)
+        vin[:half].copy_(g.pack(v[:, ev]))
+        vin[half:].copy_(g.pack(v[:, od]))
+        g.hisq.hisq_dslash_full(g.fat, g.naik, vin, vout, n)
+        want = g.oracle.dslash_full(v)
+        got = np.empty_like(v)
+        got[:, ev] = g.unpack(vout[:half], n)
+        got[:, od] = g.unpack(vout[half:], n)
+        assert rel_err(got, want) <= PREC_TOL[prec]
+
+
+def test_fma_peaks_are_measured():
+    """The FP32 and FP64 FMA throughput the ALU-bound rooflines divide by: positive, FP32 far
+    above FP64 on this part."""
+    with gpu((4, 4, 4, 4), 1, 18) as g:
+        f32, f64 = g.hisq.hisq_measure_fma_peaks()
+        assert 1.0 < f32 < 1000.0 and 0.01 < f64 < 1000.0 and f32 > 4 * f64
