@@ -1,5 +1,5 @@
-"""Plain FP64 CPU oracle of the even-odd HISQ Dslash, A = m^2 - D_eo D_oe, CG, flexible CG
-and the gauge-covariant preconditioner network (C library loaded through ctypes).
+"""Plain FP64 CPU oracle of the even-odd HISQ Dslash, A = m^2 - D_eo D_oe, CG, multi-shift CG,
+flexible CG and the gauge-covariant preconditioner network (C library loaded through ctypes).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may use it; the CUDA library never does.  It shares no code with the CUDA
@@ -48,6 +48,9 @@ def _bind(so):
     so.oracle_pc_loss_grad_normal.restype = ctypes.c_double
     so.oracle_fcg.argtypes = [_I4, _D, _D, ctypes.c_double, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
     so.oracle_fcg.restype = ctypes.c_int
+    so.oracle_cg_multishift.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
+    so.oracle_cg_multishift.restype = ctypes.c_int
     return so
 
 
@@ -185,6 +188,21 @@ class Oracle:
         it = self._so.oracle_fcg(self._L, _p(self.X), _p(self.N), float(mass), _p(W), _p(b), _p(x),
                                  float(tol), int(max_iter), ctypes.byref(rel))
         return x, it, rel.value
+
+    def cg_multishift(self, b, shifts, mass: float, tol: float = 1e-10, max_iter: int = 10000):
+        """Multi-shift CG: x_j = (A + shifts[j])^{-1} b from one Krylov space.  Returns
+        (x [nshift][V/2][3], base iterations or -1, per-shift stop iterations, per-shift true
+        relative residuals)."""
+        b = _c(b).reshape(self.V // 2, 3)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64).reshape(-1)
+        ns = sh.size
+        x = np.empty((ns, self.V // 2, 3), dtype=np.complex128)
+        its = np.zeros(ns, dtype=np.int32)
+        rel = np.zeros(ns)
+        it = self._so.oracle_cg_multishift(self._L, _p(self.X), _p(self.N), float(mass), _p(b), ns, _p(sh),
+                                           _p(x), float(tol), int(max_iter),
+                                           its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(rel))
+        return x, it, its, rel
 
 
 def adam_step(theta, grad, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):

@@ -1,6 +1,7 @@
 /*
  * Plain FP64 CPU oracle for the even-odd HISQ Dslash, the even-parity operator
- * A = m^2 - D_eo D_oe, conjugate gradient, and the gauge-covariant preconditioner network.
+ * A = m^2 - D_eo D_oe, conjugate gradient, multi-shift conjugate gradient, and the
+ * gauge-covariant preconditioner network.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct statement of what the
  * CUDA library computes.  It shares no code, header, table or helper with the CUDA path;
@@ -576,4 +577,100 @@ int oracle_fcg(const int L[4], const double *X, const double *N, double mass, co
 done:
     free(r); free(r_old); free(z); free(p); free(Ap);
     return iters;
+}
+
+/*
+ * Multi-shift conjugate gradient (Jegerlehner 1996, hep-lat/9612014; the shifted-system solver
+ * of rational-approximation workflows, not part of the paper): x_j = (A + sigma_j)^{-1} b for
+ * nshift shifts sigma_j > -m^2, all from the Krylov space of one Hestenes-Stiefel CG on the
+ * base system A + sigma_base, sigma_base = min_j sigma_j.  Every shifted residual is a multiple
+ * of the base residual, r_j = zeta_j r; with s_j = sigma_j - sigma_base, alpha, beta the base
+ * coefficients of this and (alpha_prev, beta_prev) the previous iteration:
+ *   zeta_j^new = zeta_j zeta_j^old alpha_prev
+ *                / (zeta_j^old alpha_prev (1 + s_j alpha) + alpha beta_prev (zeta_j^old - zeta_j)),
+ *   alpha_j = alpha zeta_j^new / zeta_j,   x_j += alpha_j p_j,
+ *   beta_j = beta (zeta_j^new / zeta_j)^2,   p_j = zeta_j^new r^new + beta_j p_j,
+ * starting from zeta = zeta^old = 1, alpha_prev = 1, beta_prev = 0, p_j = b, x_j = 0.  Shift j
+ * stops (x_j frozen) once |zeta_j| |r| <= tol |b| and its true residual |b - (A + sigma_j) x_j|
+ * recomputed in FP64 confirms tol; the base iterates until every shift has stopped.
+ * b: [V/2][3][2]; x: [nshift][V/2][3][2]; iters[j]: the iteration at which shift j stopped
+ * (-1 if it never did); true_rel[j]: its final true relative residual.  Returns the number of
+ * base iterations, or -1 when max_iter was reached first.
+ */
+int oracle_cg_multishift(const int L[4], const double *X, const double *N, double mass, const double *b,
+                         int nshift, const double *shifts, double *x, double tol, int max_iter, int *iters,
+                         double *true_rel) {
+    long Vh = volume(L) / 2, n = Vh * 3;
+    double *r = (double *)malloc(sizeof(double) * n * 2);
+    double *p = (double *)malloc(sizeof(double) * n * 2);
+    double *Ap = (double *)malloc(sizeof(double) * n * 2);
+    double *ps = (double *)malloc(sizeof(double) * n * 2 * nshift);
+    double *zeta = (double *)malloc(sizeof(double) * nshift * 3);
+    double *zeta_old = zeta + nshift, *zeta_new = zeta + 2 * nshift;
+    int *live = (int *)malloc(sizeof(int) * nshift);
+    double sigma_base = shifts[0];
+    for (int j = 1; j < nshift; j++)
+        if (shifts[j] < sigma_base) sigma_base = shifts[j];
+    const double mass_base = sqrt(mass * mass + sigma_base);
+    double bnorm = sqrt(norm2(b, n));
+    memcpy(r, b, sizeof(double) * n * 2);
+    memcpy(p, b, sizeof(double) * n * 2);
+    for (int j = 0; j < nshift; j++) {
+        memcpy(ps + (long)j * n * 2, b, sizeof(double) * n * 2);
+        memset(x + (long)j * n * 2, 0, sizeof(double) * n * 2);
+        zeta[j] = zeta_old[j] = 1.0;
+        live[j] = 1;
+        iters[j] = -1;
+        true_rel[j] = 1.0;
+    }
+    int result = -1, remaining = nshift;
+    if (bnorm == 0.0) {
+        for (int j = 0; j < nshift; j++) { iters[j] = 0; true_rel[j] = 0.0; }
+        result = 0;
+        remaining = 0;
+    }
+    double rr = norm2(r, n), alpha_prev = 1.0, beta_prev = 0.0;
+    for (int k = 1; k <= max_iter && remaining > 0; k++) {
+        oracle_aop(L, X, N, mass_base, p, Ap, 1);
+        double alpha = rr / dot(p, Ap, n).re;
+        for (int j = 0; j < nshift; j++) {
+            if (!live[j]) continue;
+            double s = shifts[j] - sigma_base;
+            zeta_new[j] = zeta[j] * zeta_old[j] * alpha_prev /
+                          (zeta_old[j] * alpha_prev * (1.0 + s * alpha) + alpha * beta_prev * (zeta_old[j] - zeta[j]));
+            double alpha_j = alpha * zeta_new[j] / zeta[j];
+            double *xj = x + (long)j * n * 2, *pj = ps + (long)j * n * 2;
+            for (long i = 0; i < 2 * n; i++) xj[i] += alpha_j * pj[i];
+        }
+        for (long i = 0; i < 2 * n; i++) r[i] -= alpha * Ap[i];
+        double rr_new = norm2(r, n);
+        double beta = rr_new / rr;
+        for (int j = 0; j < nshift; j++) {
+            if (!live[j]) continue;
+            double ratio = zeta_new[j] / zeta[j];
+            double beta_j = beta * ratio * ratio;
+            double *pj = ps + (long)j * n * 2;
+            for (long i = 0; i < 2 * n; i++) pj[i] = zeta_new[j] * r[i] + beta_j * pj[i];
+            zeta_old[j] = zeta[j];
+            zeta[j] = zeta_new[j];
+            if (fabs(zeta[j]) * sqrt(rr_new) <= tol * bnorm) {
+                double *xj = x + (long)j * n * 2;
+                oracle_aop(L, X, N, sqrt(mass * mass + shifts[j]), xj, Ap, 1);
+                for (long i = 0; i < 2 * n; i++) Ap[i] = b[i] - Ap[i];
+                true_rel[j] = sqrt(norm2(Ap, n)) / bnorm;
+                if (true_rel[j] <= tol) {
+                    live[j] = 0;
+                    iters[j] = k;
+                    remaining--;
+                }
+            }
+        }
+        for (long i = 0; i < 2 * n; i++) p[i] = r[i] + beta * p[i];
+        rr = rr_new;
+        alpha_prev = alpha;
+        beta_prev = beta;
+        if (remaining == 0) result = k;
+    }
+    free(r); free(p); free(Ap); free(ps); free(zeta); free(live);
+    return result;
 }

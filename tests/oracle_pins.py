@@ -191,6 +191,58 @@ def pin_cg_free_field_exact(make, dims=(8, 8, 8, 8), mass=0.05, tol=1e-10):
     return it > 0 and err <= 1e-8, f"iters {it}, rel err {err:.2e}"
 
 
+MULTISHIFTS = (0.003, 0.0, 0.05, -0.004, 1.0)
+
+
+def pin_multishift_dense_solve(make, dims=(4, 4, 4, 6), mass=0.1, tol=1e-10, shifts=MULTISHIFTS):
+    """Multi-shift CG: every x_j agrees with a dense direct solve of A + sigma_j (A assembled from
+    Eq. (3)), within its condition number times tol, and meets the true residual; the shifts are
+    unsorted and one is negative (sigma > -m^2), so the base system is not the first one."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    b = hi.gaussian_rhs(lat, 1)
+    xs, it, its, rels = o.cg_multishift(b, shifts, mass, tol=tol, max_iter=2000)
+    A = dense.a_matrix(dims, X, N, mass).toarray()
+    ev = np.linalg.eigvalsh(A)
+    worst, detail = 0.0, []
+    ok = it > 0
+    for j, s in enumerate(shifts):
+        As = A + s * np.eye(A.shape[0])
+        xd = np.linalg.solve(As, b.ravel())
+        kappa = (ev[-1] + s) / (ev[0] + s)
+        err = _rel(xs[j].ravel(), xd)
+        true = np.linalg.norm(b.ravel() - As @ xs[j].ravel()) / np.linalg.norm(b)
+        ok &= its[j] > 0 and true <= tol * 1.01 and rels[j] <= tol and err <= kappa * tol
+        worst = max(worst, err / (kappa * tol))
+        detail.append(its[j])
+    # the base (smallest shift) is the slowest system: it stops last
+    ok &= its[int(np.argmin(shifts))] == it
+    return bool(ok), f"base iters {it}, per shift {detail}, worst err/(kappa tol) {worst:.2f}"
+
+
+def pin_multishift_free_field_exact(make, dims=(8, 8, 8, 8), mass=0.05, tol=1e-10, shifts=(0.0, 0.02, 0.3, 2.0)):
+    """Multi-shift CG on the unit-link field reproduces x_j = sum c_p f_p / (lambda_p + sigma_j)
+    for a right-hand side made of a few plane waves (closed-form eigenvalues)."""
+    lat = hi.Lattice(dims)
+    c1, c3 = 9.0 / 8.0, -1.0 / 24.0
+    X, N = hi.free_field_links(lat, c1, c3)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(16)
+    b = np.zeros((lat.half_volume, 3), dtype=np.complex128)
+    x_exact = np.zeros((len(shifts), lat.half_volume, 3), dtype=np.complex128)
+    for _ in range(6):
+        k = [int(rng.integers(0, d)) for d in dims]
+        lam, p = free_field_eigenvalue(dims, k, mass, c1, c3)
+        coef = complex(rng.standard_normal(), rng.standard_normal())
+        f = plane_wave_even(lat, p, int(rng.integers(0, 3)))
+        b += coef * f
+        for j, s in enumerate(shifts):
+            x_exact[j] += coef * f / (lam + s)
+    xs, it, its, rels = o.cg_multishift(b, shifts, mass, tol=tol, max_iter=2000)
+    errs = [_rel(xs[j], x_exact[j]) for j in range(len(shifts))]
+    return it > 0 and max(errs) <= 1e-8, f"iters {it} {list(its)}, rel errs {max(errs):.2e}"
+
+
 def network_weights_identity():
     """Weights with only the identity path of channel 0 set: the network is the identity."""
     W1 = np.zeros((17, 4, 1), complex); W1[0, 0, 0] = 1
@@ -337,6 +389,7 @@ def pin_network_normal_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=16, tol=1e-
 ALL_PINS = [
     pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
     pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
+    pin_multishift_dense_solve, pin_multishift_free_field_exact,
     pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd, pin_network_loss_zero_at_inverse,
     pin_fcg_identity_is_cg, pin_network_adjoint, pin_network_normal_gradient_fd,
 ]

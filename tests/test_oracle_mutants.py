@@ -1,7 +1,7 @@
 """Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the pins catch
 every one of them: a dropped term, a wrong sign, a wrong hop length or site, a transposed
 operand, a wrong mass term and a wrong CG coefficient, a missing conjugation in the adjoint
-network, a dropped term of the normal-form gradient."""
+network, a dropped term of the normal-form gradient, wrong multi-shift recurrences."""
 import os
 import tempfile
 
@@ -32,6 +32,10 @@ MUTANTS = {
     "network_adjoint_sign": ("cplx wc = {w[0], -w[1]};", "cplx wc = {w[0], w[1]};"),
     "network_backward_hop_forward": ("long y = hop(L, x, mu, -step);", "long y = hop(L, x, mu, step);"),
     "network_adjoint_not_conjugated": ("cplx wc = c_conj((cplx){w[0], w[1]});", "cplx wc = (cplx){w[0], w[1]};"),
+    "multishift_zeta_shift_sign": ("(1.0 + s * alpha)", "(1.0 - s * alpha)"),
+    "multishift_beta_not_squared": ("double beta_j = beta * ratio * ratio;", "double beta_j = beta * ratio;"),
+    "multishift_alpha_ratio_inverted": ("double alpha_j = alpha * zeta_new[j] / zeta[j];",
+                                        "double alpha_j = alpha * zeta[j] / zeta_new[j];"),
     "normal_loss_missing_n_dag_term": ("oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */",
                                        "/* dropped */"),
 }
