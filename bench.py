@@ -43,11 +43,13 @@ def parse():
     ap.add_argument("--dims", default=DEFAULT_DIMS)
     ap.add_argument("--mass", type=float, default=DEFAULT_MASS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cg", choices=["cg", "sweep", "learned", "batch", "production"],
+    ap.add_argument("--mode", default="cg",
+                    choices=["cg", "sweep", "learned", "batch", "production", "multishift"],
                     help="cg: the benchmark line; sweep: Dslash throughput against the number of "
                          "right-hand sides; learned: the learned-preconditioner workload (32^3 x 8); "
                          "batch: bundles with uneven convergence (48^3 x 12); production: a sweep of "
-                         "Z2-noise right-hand sides (64^3 x 16)")
+                         "Z2-noise right-hand sides (64^3 x 16); multishift: eight shifted systems "
+                         "from one multi-shift solve against separate solves (32^3 x 8)")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--test-rhs", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
@@ -835,8 +837,94 @@ def production_pc(args, hisq, torch, hi, lat, X, N, mass, d64):
     return out
 
 
+MS_SHIFTS = (0.0,) + tuple(float(v) for v in 10.0 ** np.linspace(-4.0, 0.0, 7))
+
+
+def _multishift(hisq, torch, fat, naik, b, shifts, mass, **params):
+    """One hisq_cg_multishift call: (wall seconds around the synchronous call, stats, per-shift
+    iterations, per-shift FP64 true residuals)."""
+    p = hisq.hisq_default_solver_params()
+    for k, v in params.items():
+        setattr(p, k, v)
+    hisq.hisq_set_solver_params(p)
+    xs = [torch.zeros_like(b) for _ in shifts]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hisq.hisq_cg_multishift(fat, naik, b, xs, shifts, mass, TOL, raise_on_error=False)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    iters = np.zeros(len(shifts), dtype=np.int32)
+    res = np.zeros(len(shifts))
+    st = hisq.hisq_last_stats(iters, res)
+    return sec, st, iters, res
+
+
+def run_multishift(args):
+    """Eight shifted systems (A + sigma_j) x_j = b on 32^3 x 8, m = 0.01, sigma = 0 and 1e-4..1
+    (log-spaced, the spread of a rational approximation's poles), one Gaussian right-hand side,
+    every shift to the FP64 true residual 1e-10: one multi-shift solve (low-precision shared
+    iteration plus per-shift FP64 refinement, for each storage precision and shared tolerance;
+    and all in FP64) against eight separate mixed-precision CG solves."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims = tuple(int(x) for x in args.dims.split(","))
+    mass = args.mass
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    hisq.hisq_init(dims, 0, torch.cuda.current_stream())
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    b = d64(hi.gaussian_rhs(lat, 7000))
+    shifts = MS_SHIFTS
+    rows = []
+    for prec_name in ("fp16", "fp32", "fp64"):
+        prec = PREC[prec_name]
+        fat = hisq.hisq_links_create(d64(X), False, prec, 18)
+        naik = hisq.hisq_links_create(d64(N), True, prec, 18)
+        tols = (1e-3, 1e-4, 1e-5) if prec in (2, 3) else (1e-5, 1e-6, 1e-7) if prec == 1 else (None,)
+        for tol_ms in tols:
+            extra = {"multishift_tol": tol_ms} if tol_ms else {}
+            _multishift(hisq, torch, fat, naik, b, shifts, mass, inner_prec=prec, **extra)  # warm-up, capture
+            runs = [_multishift(hisq, torch, fat, naik, b, shifts, mass, inner_prec=prec, **extra) for _ in range(3)]
+            sec, st, iters, res = sorted(runs, key=lambda r: r[0])[1]
+            rows.append({"solver": "multishift", "storage": prec_name, "shared_tol": tol_ms, "seconds": sec,
+                         "shared_seconds": st.shared_seconds, "shared_iterations": int(st.shared_iterations),
+                         "refine_iterations": int(st.refine_iterations), "iterations": iters.tolist(),
+                         "converged": int(st.converged), "max_true_residual": float(res.max())})
+            print(json.dumps(rows[-1]), flush=True)
+        if prec != 0:
+            # the same eight systems as separate mixed-precision CG solves (mass sqrt(m^2 + sigma))
+            tot, its, conv, worst = 0.0, [], 0, 0.0
+            for sg in shifts:
+                m_j = float(np.sqrt(mass * mass + sg))
+                _solve_set(hisq, torch, fat, naik, [b], m_j, inner_prec=prec, bundle=1)
+                sec, st, it, res = _solve_set(hisq, torch, fat, naik, [b], m_j, inner_prec=prec, bundle=1)
+                tot += sec
+                its.append(int(it[0]))
+                conv += st.converged
+                worst = max(worst, float(res[0]))
+            rows.append({"solver": "separate_cg", "storage": prec_name, "seconds": tot, "iterations": its,
+                         "converged": conv, "max_true_residual": worst})
+            print(json.dumps(rows[-1]), flush=True)
+        hisq.hisq_links_destroy(fat)
+        hisq.hisq_links_destroy(naik)
+    best = min((r for r in rows if r["solver"] == "multishift" and r["converged"] == len(shifts)),
+               key=lambda r: r["seconds"])
+    sep = min((r for r in rows if r["solver"] == "separate_cg"), key=lambda r: r["seconds"])
+    line = {"mode": "multishift", "lattice": list(dims), "mass": mass, "shifts": list(shifts), "runs": rows,
+            "best_multishift": {k: best[k] for k in ("storage", "shared_tol", "seconds")},
+            "best_separate_cg": {k: sep[k] for k in ("storage", "seconds")},
+            "speedup_vs_separate_cg": sep["seconds"] / best["seconds"]}
+    print(json.dumps(line), flush=True)
+    hisq.hisq_finalize()
+
+
 def main():
     args = parse()
+    if args.mode == "multishift":
+        run_multishift(args)
+        return
     if args.mode == "sweep":
         run_sweep(args)
         return

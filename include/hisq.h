@@ -65,6 +65,7 @@ typedef enum { HISQ_FP64 = 0, HISQ_FP32 = 1, HISQ_FP16 = 2, HISQ_BF16 = 3 } hisq
 #define HISQ_MAX_BUNDLE 16   /* right-hand sides per solver bundle */
 #define HISQ_MAX_NRHS 64     /* right-hand sides per hisq_dslash / hisq_aop call */
 #define HISQ_PC_WEIGHTS 408  /* complex weights of the preconditioner network */
+#define HISQ_MAX_SHIFTS 16   /* shifts per multi-shift solve */
 
 typedef struct hisq_links hisq_links;
 typedef struct hisq_pc hisq_pc;
@@ -205,6 +206,9 @@ typedef struct {
                              |r|^2 together; beta from |r - alpha A p|^2 = alpha^2 |A p|^2 - |r|^2),
                              three grid barriers an iteration; 0 the two-reduction form of the
                              other drivers, four barriers */
+    double multishift_tol; /* hisq_cg_multishift with inner_prec != FP64: relative residual to
+                             which the shared low-precision iteration runs before the per-shift
+                             FP64 refinement; 0 (default) = 1e-6 for FP32, 1e-4 for FP16/BF16 */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);
@@ -219,6 +223,22 @@ int hisq_get_solver_params(hisq_solver_params *p);
  * side misses tol within max_iter. */
 int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *const rhs[],
                   double *x[], int nrhs, double mass, double tol);
+
+/* Multi-shift CG (Jegerlehner, hep-lat/9612014; the shifted solves of rational approximations,
+ * which the paper does not treat): x_j = (A + shifts[j])^{-1} rhs for j < nshift
+ * (1..HISQ_MAX_SHIFTS), every shift to the relative FP64 true residual
+ * |b - (A + shifts[j]) x_j| / |b| <= tol.  One CG iteration on the smallest shift (one A p) serves
+ * all shifts: their residuals stay multiples of its residual.  With inner_prec FP64 the iteration
+ * runs in FP64 until every shift meets tol.  Otherwise it runs in the inner precision (links
+ * packed in it) until every shift's recursive residual meets max(tol, multishift_tol), and each
+ * shift is then refined by defect correction: its FP64 residual is solved by the mixed-precision
+ * CG of hisq_cg_solve (mass sqrt(mass^2 + shifts[j])) and the correction added, until the FP64
+ * true residual meets tol.  rhs, x[j]: host or device canonical double[V/2][3][2]; shifts: host
+ * double[nshift], each > -mass^2, any order.  hisq_last_stats then reports per shift:
+ * iterations[j] = shared iterations until shift j met its recursive residual plus its
+ * refinement iterations, and true_residual[j].  Errors as hisq_cg_solve. */
+int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik, const double *rhs, double *x[],
+                       int nshift, const double *shifts, double mass, double tol);
 
 typedef struct {
     int nrhs;
@@ -246,11 +266,14 @@ typedef struct {
                                  [1] A p = m^2 p - D_eo t with <p, A p>, [2] the p, x, r update
                                  with |r|^2, [3] FP64 residual recomputations, [4] unused (0: the
                                  direction p = r + beta p is formed inside phases 0-2) */
+    int shared_iterations;    /* hisq_cg_multishift: iterations of the shared multi-shift CG */
+    long refine_iterations;   /* hisq_cg_multishift: CG iterations of the per-shift refinements */
+    double shared_seconds;    /* hisq_cg_multishift: wall time of the shared iteration */
 } hisq_solve_stats;
 
-/* Statistics of the calling thread's last hisq_cg_solve.  iterations (int[nrhs]) and
- * true_residual (double[nrhs], FP64 |b - A x| / |b| per right-hand side) are host arrays or
- * NULL. */
+/* Statistics of the calling thread's last hisq_cg_solve or hisq_cg_multishift.  iterations
+ * (int[nrhs]) and true_residual (double[nrhs], FP64 |b - A x| / |b| per right-hand side, or per
+ * shift) are host arrays or NULL. */
 int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual);
 
 /* Pick and cache the fastest Dslash launch shape for nrhs right-hand sides in the links'

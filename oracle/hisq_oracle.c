@@ -644,11 +644,11 @@ int oracle_cg_multishift(const int L[4], const double *X, const double *N, doubl
         }
         for (long i = 0; i < 2 * n; i++) r[i] -= alpha * Ap[i];
         double rr_new = norm2(r, n);
-        double beta = rr_new / rr;
+        double beta_base = rr_new / rr;
         for (int j = 0; j < nshift; j++) {
             if (!live[j]) continue;
             double ratio = zeta_new[j] / zeta[j];
-            double beta_j = beta * ratio * ratio;
+            double beta_j = beta_base * ratio * ratio;
             double *pj = ps + (long)j * n * 2;
             for (long i = 0; i < 2 * n; i++) pj[i] = zeta_new[j] * r[i] + beta_j * pj[i];
             zeta_old[j] = zeta[j];
@@ -665,10 +665,10 @@ int oracle_cg_multishift(const int L[4], const double *X, const double *N, doubl
                 }
             }
         }
-        for (long i = 0; i < 2 * n; i++) p[i] = r[i] + beta * p[i];
+        for (long i = 0; i < 2 * n; i++) p[i] = r[i] + beta_base * p[i];
         rr = rr_new;
         alpha_prev = alpha;
-        beta_prev = beta;
+        beta_prev = beta_base;
         if (remaining == 0) result = k;
     }
     free(r); free(p); free(Ap); free(ps); free(zeta); free(live);

@@ -512,7 +512,11 @@ int hisq_links_destroy(hisq_links *h) {
     if (h->scale) cudaFree(h->scale);
     if (h->words64) cudaFree(h->words64);
     hisq_ctx *ctx = h->ctx;
-    if (ctx) ctx->links.erase(std::remove(ctx->links.begin(), ctx->links.end(), h), ctx->links.end());
+    if (ctx) {
+        ctx->links.erase(std::remove(ctx->links.begin(), ctx->links.end(), h), ctx->links.end());
+        // captured graphs hold the links' device pointers: a later handle may reuse this address
+        ctx->tune_generation++;
+    }
     delete h;
     return HISQ_OK;
 }
@@ -529,6 +533,7 @@ int hisq_finalize(void) {
         free_pc(pc);
     }
     free_workspace(ctx);
+    free_multishift(ctx);
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->tmp) cudaFree(ctx->tmp);
     if (ctx->counter) cudaFree(ctx->counter);

@@ -283,6 +283,7 @@ inline size_t staged_smem(int words_per_site, int TS, int threads, int n, bool r
 }
 
 struct Workspace;  // solver workspace (solver.cu)
+struct MsWork;     // multi-shift solver workspace (multishift.cu)
 
 }  // namespace hisq
 
@@ -304,6 +305,7 @@ struct hisq_ctx {
     void *tmp;              // odd-parity intermediate for hisq_aop
     size_t tmp_cap;
     hisq::Workspace *ws;
+    hisq::MsWork *ms = nullptr;
     // last solve statistics
     hisq_solve_stats stats;
     std::vector<int> stat_iters;
@@ -356,6 +358,7 @@ LaunchShape default_shape(int prec, int n);
 LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64);
 int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64);  // tune.cu
 void free_workspace(hisq_ctx *ctx);  // solver.cu
+void free_multishift(hisq_ctx *ctx); // multishift.cu
 void free_pc(hisq_pc *pc);           // pc.cu
 int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
                void *out, int n, cudaStream_t st);

@@ -13,6 +13,7 @@ FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 MAX_BUNDLE = 16
 MAX_NRHS = 64
 PC_WEIGHTS = 408
+MAX_SHIFTS = 16
 
 STATUS = {0: "HISQ_OK", -1: "HISQ_ERR_ARG", -2: "HISQ_ERR_CUDA", -3: "HISQ_ERR_NOMEM",
           -4: "HISQ_ERR_NOT_CONVERGED", -5: "HISQ_ERR_BREAKDOWN", -6: "HISQ_ERR_TIMEOUT",
@@ -33,7 +34,7 @@ class hisq_solver_params(ctypes.Structure):
                 ("pc", ctypes.c_void_p), ("stall_window", ctypes.c_int), ("stall_factor", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("debug_barrier_timeout", ctypes.c_int), ("persistent_threads", ctypes.c_int),
-                ("single_reduction", ctypes.c_int)]
+                ("single_reduction", ctypes.c_int), ("multishift_tol", ctypes.c_double)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -45,7 +46,9 @@ class hisq_solve_stats(ctypes.Structure):
                 ("dslash_launches", ctypes.c_int), ("dslash64_ms", ctypes.c_double),
                 ("dslash64_launches", ctypes.c_int), ("flops", ctypes.c_double),
                 ("kernel_launches", ctypes.c_long), ("solve_kernel_ms", ctypes.c_double),
-                ("solve_kernel_launches", ctypes.c_int), ("phase_ms", ctypes.c_double * 5)]
+                ("solve_kernel_launches", ctypes.c_int), ("phase_ms", ctypes.c_double * 5),
+                ("shared_iterations", ctypes.c_int), ("refine_iterations", ctypes.c_long),
+                ("shared_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -74,6 +77,7 @@ _SIGNATURES = {
     "hisq_set_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_cg_solve": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _D, _D], _I),
+    "hisq_cg_multishift": ([_VP, _VP, _VP, ctypes.POINTER(_VP), _I, ctypes.POINTER(_D), _D, _D], _I),
     "hisq_last_stats": ([ctypes.POINTER(hisq_solve_stats), _VP, _VP], _I),
     "hisq_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "hisq_set_launch_shape": ([_I, _I, _I, _I, _I, _I], _I),
@@ -214,6 +218,20 @@ def hisq_cg_solve(fat, naik, rhs, x, mass: float, tol: float, raise_on_error: bo
     rp = (_VP * n)(*[_ptr(b).value for b in rhs])
     xp = (_VP * n)(*[_ptr(v).value for v in x])
     rc = load().hisq_cg_solve(fat, naik, rp, xp, n, float(mass), float(tol))
+    if raise_on_error:
+        _check(rc)
+    return rc
+
+
+def hisq_cg_multishift(fat, naik, rhs, x, shifts, mass: float, tol: float, raise_on_error: bool = True) -> int:
+    """rhs: one buffer; x: a sequence of per-shift buffers (host numpy or device tensors);
+    shifts: the per-shift sigma_j (host)."""
+    n = len(x)
+    if len(shifts) != n:
+        raise ValueError("one output buffer per shift")
+    xp = (_VP * n)(*[_ptr(v).value for v in x])
+    sh = (_D * n)(*[float(v) for v in shifts])
+    rc = load().hisq_cg_multishift(fat, naik, _ptr(rhs), xp, n, sh, float(mass), float(tol))
     if raise_on_error:
         _check(rc)
     return rc

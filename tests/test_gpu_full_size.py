@@ -137,3 +137,25 @@ def test_network_forward_32c8():
             g.hisq.hisq_pc_destroy(pc)
         want = np.stack([g.oracle.pc_forward(W, r[k]) for k in range(2)])
         assert rel_err(got, want) <= 3e-5
+
+
+def test_multishift_32c8_fp16_eight_shifts():
+    """The multi-shift workload: 32^3 x 8, m = 0.01, shifts 0 and 1e-4..1, FP16 shared iteration
+    with FP64 refinement: every shift to 1e-10 by the GPU's FP64 check; the oracle re-checks the
+    hardest and the lightest shift."""
+    import math
+    dims, mass = (32, 32, 32, 8), 0.01
+    shifts = (0.0,) + tuple(float(v) for v in 10.0 ** np.linspace(-4.0, 0.0, 7))
+    with gpu(dims, 2, 18) as g:
+        b = hi.gaussian_rhs(g.lat, 7000)
+        p = g.hisq.hisq_default_solver_params()
+        p.inner_prec = 2
+        g.hisq.hisq_set_solver_params(p)
+        xs = [np.zeros_like(b) for _ in shifts]
+        g.hisq.hisq_cg_multishift(g.fat, g.naik, b, xs, shifts, mass, TOL)
+        res = np.zeros(len(shifts))
+        s = g.hisq.hisq_last_stats(None, res)
+        assert s.converged == len(shifts) and np.all(res <= TOL), res
+        for j in (0, len(shifts) - 1):
+            m_j = math.sqrt(mass * mass + shifts[j])
+            assert g.oracle.true_residual(b, xs[j], m_j)[0] <= TOL * SLACK, j

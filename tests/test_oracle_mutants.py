@@ -33,7 +33,7 @@ MUTANTS = {
     "network_backward_hop_forward": ("long y = hop(L, x, mu, -step);", "long y = hop(L, x, mu, step);"),
     "network_adjoint_not_conjugated": ("cplx wc = c_conj((cplx){w[0], w[1]});", "cplx wc = (cplx){w[0], w[1]};"),
     "multishift_zeta_shift_sign": ("(1.0 + s * alpha)", "(1.0 - s * alpha)"),
-    "multishift_beta_not_squared": ("double beta_j = beta * ratio * ratio;", "double beta_j = beta * ratio;"),
+    "multishift_beta_not_squared": ("double beta_j = beta_base * ratio * ratio;", "double beta_j = beta_base * ratio;"),
     "multishift_alpha_ratio_inverted": ("double alpha_j = alpha * zeta_new[j] / zeta[j];",
                                         "double alpha_j = alpha * zeta[j] / zeta_new[j];"),
     "normal_loss_missing_n_dag_term": ("oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */",
