@@ -86,3 +86,13 @@ def cg_solve_bytes(prec: int, half_volume: int, iterations: int, reliable_update
     per = (cg_setup_bytes(prec, nrhs) + iterations * cg_iteration_bytes(prec, nrhs)
            + reliable_updates * reliable_update_bytes(prec, nrhs))
     return per * half_volume
+
+
+def multishift_iteration_bytes(prec: int, live_shifts: int) -> float:
+    """One shared multi-shift iteration per even site (one right-hand side): t = D_oe p (links;
+    p, t), A p = m^2 p - D_eo t (links; t, p, Ap), the update pass (r read and written, Ap read;
+    per live shift x_j and p_j read and written) and the direction pass (r read, p read and
+    written): 2 links + 8 P + 3 Q + 4 Q per live shift."""
+    P = VECTOR_BYTES[prec]
+    Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
+    return 2 * LINK_BYTES_18[prec] + 8 * P + 3 * Q + 4 * Q * live_shifts
