@@ -6,8 +6,9 @@
 // contiguous, equal share of the sites (every SM gets the same work) and keeps its own
 // shared-memory copy of the bundle state, evolving it identically: after a barrier every block
 // sums the same per-block partials in the same order and runs the same scalar step, so nothing
-// has to be broadcast.  The barrier is a generation counter whose wait is bounded: a block that
-// waits longer than the spin limit sets an error flag and the whole grid returns
+// has to be broadcast.  The barrier is one counter word whose bit 31 flips when every block has
+// arrived; its wait is bounded: a block that waits longer than the spin limit sets an error flag
+// and the whole grid returns
 // (HISQ_ERR_TIMEOUT on the host).  Vectors written inside the launch are read with ld.global.cg
 // (L2), never the read-only path.
 #pragma once
@@ -26,7 +27,7 @@ struct PersArgs {
     int n;
     double *partials;         // [gridDim][PERS_ND]
     SolverState *st;          // initial state in, final state out (block 0)
-    unsigned int *bar;        // [0] arrivals, [1] generation
+    unsigned int *bar;        // [0] the grid barrier's word (zero at launch)
     int *err;
     long long spin_limit;
     unsigned int expected;    // arrivals that complete a barrier (gridDim.x; more only to test timeouts)
@@ -75,6 +76,12 @@ __device__ __forceinline__ void clock_store(const PhaseClock &c, unsigned long l
 
 constexpr int PERS_ND = 3 * HISQ_MAX_BUNDLE;  // up to three dots per right-hand side
 
+// Grid barrier on one 32-bit word: block 0 adds 2^31 - (expected - 1) and every other block adds 1,
+// so the arrivals of all blocks together flip bit 31 and leave the low bits unchanged (no reset,
+// no second word, one atomic round trip).  Each block's thread 0 publishes the block's writes
+// (fence, then its arrival) and polls with acquire loads until bit 31 differs from the value its
+// own arrival saw.  The wait is bounded: past spin_limit polls the block raises the error flag
+// and the whole grid returns.
 __device__ __forceinline__ bool grid_sync(const PersArgs &a) {
     __shared__ int s_ok;
     __syncthreads();
@@ -82,25 +89,27 @@ __device__ __forceinline__ bool grid_sync(const PersArgs &a) {
         if (*reinterpret_cast<volatile int *>(a.err) != 0) {  // the grid is already giving up
             s_ok = 0;
         } else {
-        volatile unsigned int *gen = a.bar + 1;
-        const unsigned int g0 = *gen;
-        __threadfence();
-        if (atomicAdd(a.bar, 1u) == a.expected - 1) {
-            a.bar[0] = 0u;
+            const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (a.expected - 1u) : 1u;
             __threadfence();
-            atomicAdd(a.bar + 1, 1u);
-        } else {
+            const unsigned int old = atomicAdd(a.bar, inc);
             long long spins = 0;
-            while (*gen == g0) {
+            int ok = 1;
+            while (true) {
+                unsigned int cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(a.bar) : "memory");
+                if ((cur ^ old) & 0x80000000u) break;
                 if (++spins > a.spin_limit) {
                     atomicExch(a.err, 1);
+                    ok = 0;
+                    break;
+                }
+                if ((spins & 1023) == 0 && *reinterpret_cast<volatile int *>(a.err) != 0) {  // another block gave up
+                    ok = 0;
                     break;
                 }
                 __nanosleep(32);
             }
-        }
-        __threadfence();
-        s_ok = *reinterpret_cast<volatile int *>(a.err) == 0;
+            s_ok = ok && *reinterpret_cast<volatile int *>(a.err) == 0;
         }
     }
     __syncthreads();
@@ -277,6 +286,13 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
             const int s = tile * ts + sl;
             if (s >= g.Vh) break;
             Cplx<real> acc[R][3];
+            // 16-bit storage: the epilogue's own record (one 16-byte word per site and RHS) is
+            // requested before the stencil, so its L2 latency overlaps the link and neighbour
+            // loads; it is decoded after them
+            constexpr bool EARLY = EPI == EPI_AOP && PP == HISQ_FP16 && R == 1;
+            uint4 raw = make_uint4(0, 0, 0, 0);
+            if constexpr (EARLY)
+                if (act[0]) raw = __ldcg(reinterpret_cast<const uint4 *>(ax.v.data) + (size_t)s * n + r0);
             site_stencil<PP, 18, R, 1>(g, fat, naik, parity, in, s, 0, r0, act, acc);
             if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
@@ -285,7 +301,11 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
             } else if constexpr (EPI == EPI_AOP) {
                 const real m2 = (real)a.mass2;
                 Cplx<real> p[R][3];
-                ax.template load<R>(s, r0, act, p);
+                if constexpr (EARLY) {
+                    decode_fp16_record(raw, p[0]);
+                } else {
+                    ax.template load<R>(s, r0, act, p);
+                }
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     if (!act[r]) continue;

@@ -115,6 +115,17 @@ __device__ __forceinline__ T vld(const T *p) {
     else return __ldg(p);
 }
 
+// the colour vector held in one FP16 record (three __half2 and the float scale)
+__device__ __forceinline__ void decode_fp16_record(const uint4 q, Cplx<float> w[3]) {
+    const float sc = __uint_as_float(q.w);
+    const uint32_t h[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&h[c]));
+        w[c] = {f.x * sc, f.y * sc};
+    }
+}
+
 template <int P, bool COHERENT = false>
 __device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cplx<typename Prec<P>::real> w[3]) {
     if constexpr (P == HISQ_FP64) {
@@ -132,14 +143,7 @@ __device__ __forceinline__ void load_vec(const VecView<P> &v, long s, int r, Cpl
             w[c] = {x.x, x.y};
         }
     } else if constexpr (P == HISQ_FP16) {
-        uint4 q = vld<COHERENT>(reinterpret_cast<const uint4 *>(v.data) + s * v.n + r);
-        const float sc = __uint_as_float(q.w);
-        const uint32_t h[3] = {q.x, q.y, q.z};
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&h[c]));
-            w[c] = {f.x * sc, f.y * sc};
-        }
+        decode_fp16_record(vld<COHERENT>(reinterpret_cast<const uint4 *>(v.data) + s * v.n + r), w);
     } else {
         const __nv_bfloat162 *d = reinterpret_cast<const __nv_bfloat162 *>(v.data) + s * 3 * v.n + r;
 #pragma unroll

@@ -352,7 +352,7 @@ struct Workspace {
     int d2_grid = 0;               // blocks of the last A-operator launch enqueued
     unsigned int *counter = nullptr;
     double *dots = nullptr;
-    unsigned int *bar = nullptr;   // persistent solve: grid-barrier arrivals and generation
+    unsigned int *bar = nullptr;   // persistent solve: the grid barrier's counter word
     int *err = nullptr;            // persistent solve: a barrier wait ran out
     unsigned long long *phase_ns = nullptr;  // persistent solve: per-phase time (time_kernels)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
