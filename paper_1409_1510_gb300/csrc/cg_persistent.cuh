@@ -80,37 +80,35 @@ constexpr int PERS_ND = 3 * HISQ_MAX_BUNDLE;  // up to three dots per right-hand
 // so the arrivals of all blocks together flip bit 31 and leave the low bits unchanged (no reset,
 // no second word, one atomic round trip).  Each block's thread 0 publishes the block's writes
 // (fence, then its arrival) and polls with acquire loads until bit 31 differs from the value its
-// own arrival saw.  The wait is bounded: past spin_limit polls the block raises the error flag
-// and the whole grid returns.
+// own arrival saw.  The wait is bounded: past spin_limit polls the block raises the error flag and
+// returns false.  The flag is read only inside the wait (every 1024 polls), not on the way in or
+// out, so a completed barrier costs no extra memory round trip; a block whose peer gave up stops
+// at its next barrier, which can no longer complete, when it sees the flag.
 __device__ __forceinline__ bool grid_sync(const PersArgs &a) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (*reinterpret_cast<volatile int *>(a.err) != 0) {  // the grid is already giving up
-            s_ok = 0;
-        } else {
-            const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (a.expected - 1u) : 1u;
-            __threadfence();
-            const unsigned int old = atomicAdd(a.bar, inc);
-            long long spins = 0;
-            int ok = 1;
-            while (true) {
-                unsigned int cur;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(a.bar) : "memory");
-                if ((cur ^ old) & 0x80000000u) break;
-                if (++spins > a.spin_limit) {
-                    atomicExch(a.err, 1);
-                    ok = 0;
-                    break;
-                }
-                if ((spins & 1023) == 0 && *reinterpret_cast<volatile int *>(a.err) != 0) {  // another block gave up
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (a.expected - 1u) : 1u;
+        __threadfence();
+        const unsigned int old = atomicAdd(a.bar, inc);
+        long long spins = 0;
+        int ok = 1;
+        while (true) {
+            unsigned int cur;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(a.bar) : "memory");
+            if ((cur ^ old) & 0x80000000u) break;
+            if (++spins > a.spin_limit) {
+                atomicExch(a.err, 1);
+                ok = 0;
+                break;
             }
-            s_ok = ok && *reinterpret_cast<volatile int *>(a.err) == 0;
+            if ((spins & 1023) == 0 && *reinterpret_cast<volatile int *>(a.err) != 0) {  // a peer gave up
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
         }
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok;
@@ -226,7 +224,9 @@ __device__ __forceinline__ void publish_dots_k(const PersArgs &a, double *red, d
     }
 }
 
-// every block: dots[j] = sum over blocks of partials[b][j], j < ndots, in a fixed order
+// every block: dots[j] = sum over blocks of partials[b][j], j < ndots, in a fixed order.  Every
+// sum is a tree: an FP64 add is a 64-cycle dependent operation on this part, so a chain of adds
+// would cost more than the loads it follows.
 __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int ndots, double *dots) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     int np2 = 1;
@@ -234,10 +234,25 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
     const int per = blockDim.x / np2, j = tid % np2, k = tid / np2;
     double s = 0.0;
     if (j < ndots && k < per) {
-        for (int b = k; b < (int)gridDim.x; b += per) s += __ldcg(a.partials + (size_t)b * PERS_ND + j);
+        // the partials were written by other SMs just before the barrier: four independent loads
+        // at a time, then a pairwise sum
+        constexpr int U = 4;
+        for (int b0 = k; b0 < (int)gridDim.x; b0 += U * per) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int b = b0 + u * per;
+                v[u] = b < (int)gridDim.x ? __ldcg(a.partials + (size_t)b * PERS_ND + j) : 0.0;
+            }
+#pragma unroll
+            for (int w = 1; w < U; w *= 2)
+#pragma unroll
+                for (int u = 0; u < U; u += 2 * w) v[u] += v[u + w];
+            s += v[0];
+        }
     }
     for (int off = 16; off >= np2; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const int groups = np2 < 32 ? nwarps : per;
+    const int groups = np2 < 32 ? nwarps : per;  // partial sums per column (at most 32)
     __syncthreads();
     if (np2 < 32) {
         if (lane < np2) red[warp * np2 + lane] = s;
@@ -245,10 +260,11 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
         red[tid] = s;
     }
     __syncthreads();
-    if (tid < ndots) {
-        double t = 0.0;
-        for (int q = 0; q < groups; q++) t += red[q * np2 + tid];
-        dots[tid] = t;
+    for (int jj = warp; jj < ndots; jj += nwarps) {  // one warp per column: a shuffle tree
+        double t = lane < groups ? red[lane * np2 + jj] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) dots[jj] = t;
     }
     __syncthreads();
 }

@@ -444,6 +444,7 @@ void hisq_default_solver_params(hisq_solver_params *p) {
     p->autotune = 1;
     p->time_kernels = 0;
     p->single_reduction = 1;
+    p->l2_persist_links = 1;
 }
 
 int hisq_init(const int dims[4], int device, void *cuda_stream) {
@@ -534,6 +535,11 @@ int hisq_finalize(void) {
     }
     free_workspace(ctx);
     free_multishift(ctx);
+    if (ctx->l2_limit_saved) {  // give the context its L2 set-aside back as it was
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_limit_old);
+        cudaGetLastError();
+    }
     if (ctx->partials) cudaFree(ctx->partials);
     if (ctx->tmp) cudaFree(ctx->tmp);
     if (ctx->counter) cudaFree(ctx->counter);

@@ -310,6 +310,10 @@ struct hisq_ctx {
     size_t tmp_cap;
     hisq::Workspace *ws;
     hisq::MsWork *ms = nullptr;
+    // L2 persisting set-aside for the link window of the persistent solve
+    int l2_persist_max = -1, l2_window_max = 0;  // device limits (-1: not queried yet)
+    bool l2_limit_saved = false;                 // l2_limit_old holds the context's limit before ours
+    size_t l2_limit_old = 0;
     // last solve statistics
     hisq_solve_stats stats;
     std::vector<int> stat_iters;

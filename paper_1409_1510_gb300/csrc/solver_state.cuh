@@ -191,19 +191,25 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
                 st->alpha[k][0] = 0.0;
                 continue;
             }
-            const double al = g / pap;
-            double gn = al * al * apap - g;
-            if (!(gn > 0.0)) gn = 0.0;  // cancellation at convergence: the FP64 check decides
+            // one division and no square root on the critical path (an FP64 division or square
+            // root is a long dependent sequence on this part): with q = |A p|^2 / <p, A p>,
+            // beta = |r_new|^2 / |r|^2 = alpha^2 |A p|^2 / |r|^2 - 1 = alpha q - 1, and the
+            // stopping tests compare squares
+            const double inv = 1.0 / pap;
+            const double al = g * inv;
+            double be = al * (apap * inv) - 1.0;
+            if (!(be > 0.0)) be = 0.0;  // cancellation at convergence: the FP64 check decides
+            const double gn = be * g;
             st->alpha[k][0] = al;
             st->alpha[k][1] = 0.0;
             st->iters[k] += 1;
             st->rr_prev[k] = g;
-            st->beta[k][0] = gn / g;
+            st->beta[k][0] = be;
             st->beta[k][1] = 0.0;
             st->rr[k] = gn;
-            const double rn = sqrt(gn);
-            const bool at_tol = rn <= st->tol * st->bnorm[k];
-            const bool drop = (!st->inner_fp64) && rn < st->delta * st->r_upd[k];
+            const double tb = st->tol * st->bnorm[k], du = st->delta * st->r_upd[k];
+            const bool at_tol = gn <= tb * tb;
+            const bool drop = (!st->inner_fp64) && gn < du * du;
             const bool last = st->iters[k] >= st->max_iter;
             if (at_tol || drop || last) any = 1;
         }

@@ -34,7 +34,8 @@ class hisq_solver_params(ctypes.Structure):
                 ("pc", ctypes.c_void_p), ("stall_window", ctypes.c_int), ("stall_factor", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("time_kernels", ctypes.c_int),
                 ("debug_barrier_timeout", ctypes.c_int), ("persistent_threads", ctypes.c_int),
-                ("single_reduction", ctypes.c_int), ("multishift_tol", ctypes.c_double)]
+                ("single_reduction", ctypes.c_int), ("multishift_tol", ctypes.c_double),
+                ("l2_persist_links", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
