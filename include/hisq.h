@@ -234,10 +234,10 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
  * |b - (A + shifts[j]) x_j| / |b| <= tol.  One CG iteration on the smallest shift (one A p) serves
  * all shifts: their residuals stay multiples of its residual.  With inner_prec FP64 the iteration
  * runs in FP64 until every shift meets tol.  Otherwise it runs in the inner precision (links
- * packed in it) until every shift's recursive residual meets max(tol, multishift_tol), and each
- * shift is then refined by defect correction: its FP64 residual is solved by the mixed-precision
- * CG of hisq_cg_solve (mass sqrt(mass^2 + shifts[j])) and the correction added, until the FP64
- * true residual meets tol.  rhs, x[j]: host or device canonical double[V/2][3][2]; shifts: host
+ * packed in it) until every shift's recursive residual meets max(tol, multishift_tol), and the
+ * shifts are then refined by defect correction: their FP64 residuals are solved together as one
+ * bundle of shifted systems (right-hand side j with mass^2 + shifts[j]) by the mixed-precision
+ * persistent CG and the corrections added, until every FP64 true residual meets tol.  rhs, x[j]: host or device canonical double[V/2][3][2]; shifts: host
  * double[nshift], each > -mass^2, any order.  hisq_last_stats then reports per shift:
  * iterations[j] = shared iterations until shift j met its recursive residual plus its
  * refinement iterations, and true_residual[j].  Errors as hisq_cg_solve. */

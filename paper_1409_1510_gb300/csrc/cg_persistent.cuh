@@ -23,7 +23,6 @@ struct PersArgs {
     void *p, *t, *ap;         // inner precision bundles
     void *x, *r;              // x_lo and r in the iterated precision
     void *b, *xhi, *t64;      // FP64
-    double mass2;
     int n;
     double *partials;         // [gridDim][PERS_ND]
     SolverState *st;          // initial state in, final state out (block 0)
@@ -274,11 +273,11 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
 // (ax from the loader `ax` at the output site); with DOTS2 also |out|^2, published as columns
 // 2n..3n-1 (columns n..2n-1 are left to the update phase's |r|^2).  EPI_RESID (FP64):
 // r = b - m^2 ax + D in, written to out_lo (iterated precision Q) with |r|^2 per block.  mask[r]
-// selects right-hand sides.
+// selects right-hand sides; m2v[r] is the m^2 of right-hand side r (shared memory).
 template <int PP, int R, int EPI, int Q, class IN, class AX, bool DOTS2 = false>
 __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
                                              const IN &in, void *out, int parity, const int *mask, const AX &ax,
-                                             const void *bvec, void *out_lo, double *red) {
+                                             const void *bvec, void *out_lo, double *red, const double *m2v) {
     using real = typename Prec<PP>::real;
     const Geom &g = a.g;
     const int n = a.n, t = n / R, spb = blockDim.x / t;
@@ -315,7 +314,6 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                 for (int r = 0; r < R; r++)
                     if (act[r]) store_vec<PP>(vout, s, r0 + r, acc[r]);
             } else if constexpr (EPI == EPI_AOP) {
-                const real m2 = (real)a.mass2;
                 Cplx<real> p[R][3];
                 if constexpr (EARLY) {
                     decode_fp16_record(raw, p[0]);
@@ -325,6 +323,7 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     if (!act[r]) continue;
+                    const real m2 = (real)m2v[r0 + r];
                     Cplx<real> w[3];
                     real d = 0;
 #pragma unroll
@@ -354,10 +353,11 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
                     Cplx<typename Prec<Q>::real> lo3[3];
                     load_vec<HISQ_FP64, true>(vb, s, r0 + r, b);
                     double d = 0.0;
+                    const double m2 = m2v[r0 + r];
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
-                        double wr = b[c].re - a.mass2 * x[r][c].re + (double)acc[r][c].re;
-                        double wi = b[c].im - a.mass2 * x[r][c].im + (double)acc[r][c].im;
+                        double wr = b[c].re - m2 * x[r][c].re + (double)acc[r][c].re;
+                        double wi = b[c].im - m2 * x[r][c].im + (double)acc[r][c].im;
                         d += wr * wr + wi * wi;
                         lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
                     }

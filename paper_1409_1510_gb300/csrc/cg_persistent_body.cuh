@@ -70,13 +70,12 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
     while (CG1 && ok && st.any_active && st.bundle_iters < st.max_iter) {
         // t = D_oe p
         dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(p)}, a.t, 1, st.active,
-                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
+                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red, st.mass2);
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_DOE);
         // A p = m^2 p - D_eo t with <p, A p> and |A p|^2 (|r|^2 came from the previous update phase)
         dslash_phase<P, R, EPI_AOP, Q, PlainIn<P, true>, PlainIn<P, true>, true>(
-            a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active, PlainIn<P, true>{VP(p)}, nullptr, nullptr,
-            red);
+            a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active, PlainIn<P, true>{VP(p)}, nullptr, nullptr, red, st.mass2);
         if (!(ok = grid_sync(a))) break;
         sum_partials(a, red, 3 * n, dots);
         if (tid == 0) run_hook(HOOK_CG1, &st, dots, n);
@@ -133,11 +132,10 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
         if (st.any_update) {
             // r = b - A x_hi in FP64 (written to r), |r|^2; then p = r + beta p with beta from it
             dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
-                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr,
-                                                     red);
+                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red, st.mass2);
             if (!(ok = grid_sync(a))) break;
             dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
-                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red);
+                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red, st.mass2);
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, n, dots);
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
@@ -165,12 +163,12 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
     while (!CG1 && ok && st.any_active && st.bundle_iters < st.max_iter) {
         // t = D_oe p
         dslash_phase<P, R, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(p)}, a.t, 1, st.active,
-                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
+                                         PlainIn<P, true>{VP(p)}, nullptr, nullptr, red, st.mass2);
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_DOE);
         // A p = m^2 p - D_eo t and <p, A p>
         dslash_phase<P, R, EPI_AOP, Q>(a, a.fat, a.naik, PlainIn<P, true>{VP(t)}, a.ap, 0, st.active,
-                                       PlainIn<P, true>{VP(p)}, nullptr, nullptr, red);
+                                       PlainIn<P, true>{VP(p)}, nullptr, nullptr, red, st.mass2);
         if (!(ok = grid_sync(a))) break;
         sum_partials(a, red, n, dots);
         if (tid == 0) run_hook(HOOK_ALPHA, &st, dots, n);
@@ -230,11 +228,10 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
             }
             if (!(ok = grid_sync(a))) break;
             dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
-                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr,
-                                                     red);
+                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red, st.mass2);
             if (!(ok = grid_sync(a))) break;
             dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
-                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red);
+                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red, st.mass2);
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, n, dots);
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);

@@ -367,6 +367,11 @@ LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *
 int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64);  // tune.cu
 void free_workspace(hisq_ctx *ctx);  // solver.cu
 void free_multishift(hisq_ctx *ctx); // multishift.cu
+// CG solve of nrhs right-hand sides (solver.cu): hisq_cg_solve when mass2v and tolv are null;
+// otherwise each right-hand side k solves (mass2v[k] - D_eo D_oe) x = b to tolv[k] (persistent
+// driver, 18-real Naik links, no preconditioner)
+int cg_solve_common(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, const double *const rhs[],
+                    double *x[], int nrhs, double mass, double tol, const double *mass2v, const double *tolv);
 void free_pc(hisq_pc *pc);           // pc.cu
 int pc_forward(hisq_ctx *ctx, const hisq_pc *pc, const hisq_links *fat, const hisq_links *naik, const void *in,
                void *out, int n, cudaStream_t st);

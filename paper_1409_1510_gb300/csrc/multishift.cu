@@ -17,9 +17,10 @@
 // kernel (after every block has finished reading) writes the state.
 //
 // With a low-precision inner iteration (FP32 / FP16 / BF16 storage, FP32 x_j, r, p_j) the shared
-// iteration stops at a looser tolerance and every shift is refined by defect correction in FP64
-// (its true residual, solved by the mixed-precision CG with mass sqrt(m^2 + sigma_j), added),
-// until the FP64 true residual meets the requested tolerance.
+// iteration stops at a looser tolerance and the shifts are refined by defect correction in FP64:
+// their true residuals, solved together as one bundle of shifted systems (a mass per right-hand
+// side) by the mixed-precision persistent CG, and the corrections added, until every FP64 true
+// residual meets the requested tolerance.
 #include <string.h>
 #include <math.h>
 #include <chrono>
@@ -354,8 +355,8 @@ static int ms_workspace(hisq_ctx *ctx, int nshift, int prec) {
         {&w->ap, vector_bytes(prec, Vh, 1)},       {&w->xs, vector_bytes(Q, Vh, 1) * cap},
         {&w->ps, vector_bytes(Q, Vh, 1) * cap},    {&w->x64, vector_bytes(HISQ_FP64, Vh, 1)},
         {&w->t64, vector_bytes(HISQ_FP64, Vh, 1)}, {&w->r64, vector_bytes(HISQ_FP64, Vh, 1)},
-        {(void **)&w->canon_b, canon},             {(void **)&w->canon_r, canon},
-        {(void **)&w->canon_e, canon},             {(void **)&w->canon_x, canon * cap},
+        {(void **)&w->canon_b, canon},             {(void **)&w->canon_r, canon * cap},
+        {(void **)&w->canon_e, canon * cap},       {(void **)&w->canon_x, canon * cap},
     };
     for (auto &a : allocs)
         if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
@@ -625,44 +626,69 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     if (shared.breakdown) return set_error(HISQ_ERR_BREAKDOWN, "multi-shift CG breakdown (non-positive <p, A p> or NaN)");
 
     // ---- per-shift FP64 check and refinement by defect correction ----
+    // Every shift's FP64 residual r_j = b - (A + sigma_j) x_j; those above tol are solved together
+    // as one bundle of shifted systems, (m^2 + sigma_j - D_eo D_oe) e_j = r_j to 0.5 tol |b| / |r_j|,
+    // by the mixed-precision CG (persistent driver), and x_j += e_j.  b - (A + sigma_j)(x_j + e_j)
+    // = r_j - (A + sigma_j) e_j exactly, so the correction's own FP64 true residual gives the new
+    // residual of x_j; a shift still above tol is recomputed and solved again (at most three rounds).
     std::vector<int> iters(nshift, 0);
-    std::vector<double> resid(nshift, 1.0);
+    std::vector<double> resid(nshift, 0.0);
     long refine_iters = 0;
-    int worst = HISQ_OK;
     const double bb = shared.bb;
+    const bool bundled = naik->recon == 18;
+    const double *rp[HISQ_MAX_SHIFTS];
+    double *ep[HISQ_MAX_SHIFTS];
+    double m2v[HISQ_MAX_SHIFTS], tolv[HISQ_MAX_SHIFTS];
+    int idx[HISQ_MAX_SHIFTS];
     for (int j = 0; j < nshift; j++) {
-        double *xc = w->canon_x + (size_t)j * Vh * 6;
-        const double m2j = mass * mass + shifts[j];
         iters[j] = shared.stop_iter[j] >= 0 ? shared.stop_iter[j] : shared.k;
-        if (!(bb > 0.0)) {
-            HISQ_CUDA(cudaMemsetAsync(xc, 0, vbytes, st));
-            resid[j] = 0.0;
-            continue;
-        }
-        bool done = false;
-        for (int round = 0; round < 4 && !done; round++) {
+        if (!(bb > 0.0)) HISQ_CUDA(cudaMemsetAsync(w->canon_x + (size_t)j * Vh * 6, 0, vbytes, st));
+        else resid[j] = 2.0 * tol + 1.0;  // not yet measured
+    }
+    for (int round = 0; round < 3 && bb > 0.0; round++) {
+        int m = 0;
+        for (int j = 0; j < nshift; j++) {
+            if (resid[j] <= tol) continue;
             double res2 = 0.0;
-            HISQ_CHECK(ms_residual(ctx, w, fat, naik, xc, m2j, &res2));
-            const double rho = sqrt(res2 / bb);
-            resid[j] = rho;
-            if (rho <= tol) {
-                done = true;
-                break;
-            }
-            if (round == 3) break;
-            // solve (A + sigma_j) e = r_j to the relative tolerance that brings x_j + e to tol
-            HISQ_CHECK(unpack_vectors(ctx, w->r64, w->canon_r, 1, HISQ_FP64, st));
-            const double *rp[1] = {w->canon_r};
-            double *ep[1] = {w->canon_e};
-            const int rc = hisq_cg_solve(fat, naik, rp, ep, 1, sqrt(m2j), 0.5 * tol / rho);
-            refine_iters += ctx->stats.total_iterations;
-            iters[j] += ctx->stats.total_iterations;
+            HISQ_CHECK(ms_residual(ctx, w, fat, naik, w->canon_x + (size_t)j * Vh * 6, mass * mass + shifts[j], &res2));
+            resid[j] = sqrt(res2 / bb);
+            if (resid[j] <= tol) continue;
+            HISQ_CHECK(unpack_vectors(ctx, w->r64, w->canon_r + (size_t)j * Vh * 6, 1, HISQ_FP64, st));
+            idx[m] = j;
+            rp[m] = w->canon_r + (size_t)j * Vh * 6;
+            ep[m] = w->canon_e + (size_t)j * Vh * 6;
+            m2v[m] = mass * mass + shifts[j];
+            tolv[m] = 0.5 * tol / resid[j];
+            m++;
+        }
+        if (m == 0) break;
+        if (bundled) {
+            double tmin = tolv[0];
+            for (int q = 1; q < m; q++) tmin = std::min(tmin, tolv[q]);
+            const int rc = cg_solve_common(ctx, fat, naik, rp, ep, m, mass, tmin, m2v, tolv);
             if (rc != HISQ_OK && rc != HISQ_ERR_NOT_CONVERGED) return rc;
-            ms_axpy_canon_kernel<<<ms_grid(ctx), 256, 0, st>>>(xc, w->canon_e, (long)Vh * 6);
+            refine_iters += ctx->stats.total_iterations;
+            for (int q = 0; q < m; q++) {
+                iters[idx[q]] += ctx->stat_iters[q];
+                resid[idx[q]] *= ctx->stat_resid[q];
+            }
+        } else {
+            for (int q = 0; q < m; q++) {
+                const int rc = cg_solve_common(ctx, fat, naik, rp + q, ep + q, 1, sqrt(m2v[q]), tolv[q], nullptr, nullptr);
+                if (rc != HISQ_OK && rc != HISQ_ERR_NOT_CONVERGED) return rc;
+                refine_iters += ctx->stats.total_iterations;
+                iters[idx[q]] += ctx->stat_iters[0];
+                resid[idx[q]] *= ctx->stat_resid[0];
+            }
+        }
+        for (int q = 0; q < m; q++) {
+            ms_axpy_canon_kernel<<<ms_grid(ctx), 256, 0, st>>>(w->canon_x + (size_t)idx[q] * Vh * 6, ep[q], (long)Vh * 6);
             HISQ_CUDA(cudaGetLastError());
         }
-        if (!done) worst = HISQ_ERR_NOT_CONVERGED;
     }
+    int worst = HISQ_OK;
+    for (int j = 0; j < nshift; j++)
+        if (!(resid[j] <= tol)) worst = HISQ_ERR_NOT_CONVERGED;
     for (int j = 0; j < nshift; j++)
         HISQ_CUDA(cudaMemcpyAsync(x[j], w->canon_x + (size_t)j * Vh * 6, vbytes, cudaMemcpyDefault, st));
     HISQ_CUDA(cudaStreamSynchronize(st));

@@ -464,6 +464,8 @@ struct Solve {
     bool persistent = false;                                     // solved by the persistent kernel
     bool pers_timing = false;        // time the persistent kernel (CUDA events) and its phases
     hisq_solve_stats *stats = nullptr;
+    const double *mass2v = nullptr;  // per right-hand side m^2 (shifted systems; persistent driver only)
+    const double *tolv = nullptr;    // per right-hand side relative tolerance (or null: the solve's tol)
 };
 
 static BlasArgs blas_args(const Solve &S) {
@@ -647,7 +649,10 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->use_pc = S.pc != nullptr;
     h->stall_window = P.stall_window;
     h->stall_factor = P.stall_factor;
-    h->tol = tol;
+    for (int k = 0; k < S.n; k++) {
+        h->tolk[k] = S.tolv ? S.tolv[k] : tol;
+        h->mass2[k] = S.mass2v ? S.mass2v[k] : S.mass * S.mass;
+    }
     h->delta = P.delta;
     h->h_loop = h_loop;
     h->h_upd = h_upd;
@@ -865,7 +870,6 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     a.b = w->b_hi;
     a.xhi = w->x_hi;
     a.t64 = w->t64;
-    a.mass2 = S.mass * S.mass;
     a.n = S.n;
     a.partials = w->partials;
     a.st = w->st;
@@ -921,13 +925,14 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
 static int solve_bundle(Solve &S, double tol) {
     Workspace *w = S.w;
     const hisq_solver_params &P = S.ctx->params;
-    if (P.use_graph == 2 && !S.timing) {
+    if ((P.use_graph == 2 && !S.timing) || S.mass2v) {
         bool done = false;
         HISQ_CHECK(solve_bundle_persistent(S, tol, &done));
         if (done) {
             S.persistent = true;
             return HISQ_OK;
         }
+        if (S.mass2v) return set_error(HISQ_ERR_ARG, "a bundle of shifted systems needs the persistent driver");
     }
     bool graph = P.use_graph && !S.timing;
     if (graph) {
@@ -965,43 +970,17 @@ static int solve_bundle(Solve &S, double tol) {
     return HISQ_OK;
 }
 
-}  // namespace hisq
-
-using namespace hisq;
-
-extern "C" {
-
-int hisq_set_solver_params(const hisq_solver_params *p) {
-    hisq_ctx *ctx;
-    HISQ_CHECK(require_ctx(&ctx));
-    if (!p) return set_error(HISQ_ERR_ARG, "null params");
-    if (p->inner_prec < HISQ_FP64 || p->inner_prec > HISQ_BF16) return set_error(HISQ_ERR_ARG, "bad inner precision");
-    if (p->max_iter < 1) return set_error(HISQ_ERR_ARG, "max_iter must be >= 1");
-    if (!(p->delta > 0.0 && p->delta < 1.0)) return set_error(HISQ_ERR_ARG, "delta must be in (0, 1)");
-    if (p->bundle < 0 || p->bundle > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "bundle must be in 0..%d", HISQ_MAX_BUNDLE);
-    if (p->pc && p->pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
-    ctx->params = *p;
-    return HISQ_OK;
-}
-
-int hisq_get_solver_params(hisq_solver_params *p) {
-    hisq_ctx *ctx;
-    HISQ_CHECK(require_ctx(&ctx));
-    if (!p) return set_error(HISQ_ERR_ARG, "null params");
-    *p = ctx->params;
-    return HISQ_OK;
-}
-
-int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *const rhs[], double *x[], int nrhs,
-                  double mass, double tol) {
+// hisq_cg_solve, and (mass2v, tolv set) bundles of shifted systems with per-right-hand-side m^2 and
+// tolerance on the persistent driver
+int cg_solve_common(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, const double *const rhs[],
+                    double *x[], int nrhs, double mass, double tol, const double *mass2v, const double *tolv) {
     auto t0 = std::chrono::steady_clock::now();
-    hisq_ctx *ctx;
-    HISQ_CHECK(require_ctx(&ctx));
     if (!fat || !naik || !rhs || !x) return set_error(HISQ_ERR_ARG, "null argument");
     if (fat->ctx != ctx || naik->ctx != ctx) return set_error(HISQ_ERR_STATE, "links of another context");
     if (fat->is_naik || !naik->is_naik) return set_error(HISQ_ERR_ARG, "expected (fat, naik) links");
     if (nrhs < 1) return set_error(HISQ_ERR_ARG, "nrhs must be >= 1");
     if (!(tol > 0.0)) return set_error(HISQ_ERR_ARG, "tol must be positive");
+    if (mass2v && ctx->params.pc) return set_error(HISQ_ERR_ARG, "shifted bundles run without the preconditioner");
     for (int k = 0; k < nrhs; k++)
         if (!rhs[k] || !x[k]) return set_error(HISQ_ERR_ARG, "null rhs or x pointer %d", k);
     const hisq_solver_params &P = ctx->params;
@@ -1035,8 +1014,11 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
         int n = std::min(bundle, nrhs - k0);
         Solve S{ctx, w, fat, naik, n, prec, mass, ctx->stream, P.time_kernels != 0 && !P.use_graph, &events, &events64,
                 P.pc};
-        S.pers_timing = P.time_kernels != 0 && P.use_graph == 2;
+        S.pers_timing = P.time_kernels != 0 && (P.use_graph == 2 || mass2v);
         S.stats = &stats;
+        S.mass2v = mass2v ? mass2v + k0 : nullptr;
+        S.tolv = tolv ? tolv + k0 : nullptr;
+        if (mass2v) S.timing = false;  // shifted bundles run on the persistent driver only
         // tune (outside any capture) before the first use of this shape
         if (P.autotune) {
             tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64);
@@ -1095,6 +1077,40 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
                          nrhs, tol, P.max_iter);
     if (worst == HISQ_ERR_BREAKDOWN) return set_error(worst, "solver breakdown in at least one right-hand side");
     return HISQ_OK;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+int hisq_set_solver_params(const hisq_solver_params *p) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!p) return set_error(HISQ_ERR_ARG, "null params");
+    if (p->inner_prec < HISQ_FP64 || p->inner_prec > HISQ_BF16) return set_error(HISQ_ERR_ARG, "bad inner precision");
+    if (p->max_iter < 1) return set_error(HISQ_ERR_ARG, "max_iter must be >= 1");
+    if (!(p->delta > 0.0 && p->delta < 1.0)) return set_error(HISQ_ERR_ARG, "delta must be in (0, 1)");
+    if (p->bundle < 0 || p->bundle > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "bundle must be in 0..%d", HISQ_MAX_BUNDLE);
+    if (p->pc && p->pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
+    ctx->params = *p;
+    return HISQ_OK;
+}
+
+int hisq_get_solver_params(hisq_solver_params *p) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    if (!p) return set_error(HISQ_ERR_ARG, "null params");
+    *p = ctx->params;
+    return HISQ_OK;
+}
+
+int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *const rhs[], double *x[], int nrhs,
+                  double mass, double tol) {
+    hisq_ctx *ctx;
+    HISQ_CHECK(require_ctx(&ctx));
+    return cg_solve_common(ctx, fat, naik, rhs, x, nrhs, mass, tol, nullptr, nullptr);
 }
 
 int hisq_last_stats(hisq_solve_stats *s, int *iterations, double *true_residual) {

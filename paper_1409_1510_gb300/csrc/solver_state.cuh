@@ -31,6 +31,10 @@ struct SolverState {
     double r_win[HISQ_MAX_BUNDLE];    // flexible CG: |r| at the start of the stall window
     double bnorm[HISQ_MAX_BUNDLE];
     double true_res[HISQ_MAX_BUNDLE]; // last FP64 relative true residual
+    double tolk[HISQ_MAX_BUNDLE];     // relative tolerance of each right-hand side
+    double mass2[HISQ_MAX_BUNDLE];    // m^2 of each right-hand side's operator m^2 - D_eo D_oe
+                                      // (one value for a plain solve; the persistent driver also
+                                      // solves bundles of shifted systems)
     int active[HISQ_MAX_BUNDLE];      // 1 while iterating
     int update[HISQ_MAX_BUNDLE];      // 1 when an FP64 residual recomputation is due
     int iters[HISQ_MAX_BUNDLE];
@@ -50,7 +54,6 @@ struct SolverState {
     int use_pc;
     int stall_window;
     double stall_factor;
-    double tol;
     double delta;
     unsigned long long h_loop;        // conditional handles (0 when not in a graph)
     unsigned long long h_upd;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             st->beta[k][0] = be;
             st->beta[k][1] = 0.0;
             st->rr[k] = gn;
-            const double tb = st->tol * st->bnorm[k], du = st->delta * st->r_upd[k];
+            const double tb = st->tolk[k] * st->bnorm[k], du = st->delta * st->r_upd[k];
             const bool at_tol = gn <= tb * tb;
             const bool drop = (!st->inner_fp64) && gn < du * du;
             const bool last = st->iters[k] >= st->max_iter;
@@ -238,7 +241,7 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
                 continue;
             }
             double rn = sqrt(rr);
-            bool at_tol = rn <= st->tol * st->bnorm[k];
+            bool at_tol = rn <= st->tolk[k] * st->bnorm[k];
             bool drop = (!st->inner_fp64) && rn < st->delta * st->r_upd[k];
             bool last = st->iters[k] >= st->max_iter;
             if (at_tol || drop || last) {
@@ -295,7 +298,7 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             }
             double rn = sqrt(r2);
             st->true_res[k] = rn / st->bnorm[k];
-            if (st->true_res[k] <= st->tol) {
+            if (st->true_res[k] <= st->tolk[k]) {
                 st->active[k] = 0;
                 st->status[k] = RHS_CONVERGED;
             } else if (st->iters[k] >= st->max_iter) {
