@@ -210,9 +210,9 @@ typedef struct {
                              which the shared low-precision iteration runs before the per-shift
                              FP64 refinement; 0 (default) = 1e-6 for FP32, 1e-4 for FP16/BF16 */
     int l2_persist_links; /* persistent driver: 1 (default) keeps the inner-precision Naik links
-                             resident in L2 during the solve (stream access-policy window over
-                             them, persisting set-aside up to the device's limit, released after
-                             the solve and restored by hisq_finalize); 0 = plain caching */
+                             resident in L2 during the solve when they fit the device's persisting
+                             set-aside (stream access-policy window over them, released after the
+                             solve, the set-aside restored by hisq_finalize); 0 = plain caching */
 } hisq_solver_params;
 
 void hisq_default_solver_params(hisq_solver_params *p);

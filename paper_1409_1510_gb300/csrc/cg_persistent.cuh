@@ -277,11 +277,14 @@ __device__ __forceinline__ void sum_partials(const PersArgs &a, double *red, int
 template <int PP, int R, int EPI, int Q, class IN, class AX, bool DOTS2 = false>
 __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField &fat, const LinkField &naik,
                                              const IN &in, void *out, int parity, const int *mask, const AX &ax,
-                                             const void *bvec, void *out_lo, double *red, const double *m2v) {
+                                             const void *bvec, void *out_lo, double *red, const double *m2v,
+                                             const int *list = nullptr, int nlist = 0) {
     using real = typename Prec<PP>::real;
     const Geom &g = a.g;
-    const int n = a.n, t = n / R, spb = blockDim.x / t;
-    const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = gi * R;
+    // with a list (R = 1), one thread per (site, listed right-hand side): a pass over u of the
+    // bundle's n right-hand sides costs u / n of a full pass instead of idling n - u lanes
+    const int n = a.n, t = list ? nlist : n / R, spb = blockDim.x / t;
+    const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = list ? list[gi] : gi * R;
     const VecView<PP> vout{out, n};
     bool act[R];
     bool any = false;
@@ -370,7 +373,7 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
     if constexpr (DOTS2) {
         publish_dots_k<R, 2>(a, red, dot, t, gi, n, 2 * n);
     } else if constexpr (EPI != EPI_PLAIN) {
-        publish_dots<R>(a, red, dot[0], t, gi, n);
+        publish_dots<R>(a, red, dot[0], t, gi, list ? nlist : n);  // with a list: column i = list[i]
     }
 }
 

@@ -13,6 +13,7 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
     __shared__ SolverState st;
     __shared__ double dots[PERS_ND];
     __shared__ PhaseClock clk;
+    __shared__ int upd_list[HISQ_MAX_BUNDLE], upd_n;  // right-hand sides of an FP64 recomputation
     const int tid = threadIdx.x, n = a.n;
     {
         constexpr int WORDS = sizeof(SolverState) / sizeof(uint32_t);
@@ -130,15 +131,29 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
         if (!(ok = grid_sync(a))) break;
         clock_mark(clk, PH_UPDATE);
         if (st.any_update) {
-            // r = b - A x_hi in FP64 (written to r), |r|^2; then p = r + beta p with beta from it
+            // r = b - A x_hi in FP64 (written to r), |r|^2; then p = r + beta p with beta from it.
+            // Only the right-hand sides due for it take part (the FP64 passes are FP64-arithmetic
+            // bound, so their cost follows the number of such right-hand sides)
+            if (tid == 0) {
+                int u = 0;
+                for (int k = 0; k < n; k++)
+                    if (st.update[k]) upd_list[u++] = k;
+                upd_n = u;
+            }
+            __syncthreads();
             dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
-                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red, st.mass2);
+                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red,
+                                                     st.mass2, upd_list, upd_n);
             if (!(ok = grid_sync(a))) break;
             dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
-                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red, st.mass2);
+                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red,
+                                                     st.mass2, upd_list, upd_n);
             if (!(ok = grid_sync(a))) break;
-            sum_partials(a, red, n, dots);
-            if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
+            sum_partials(a, red, upd_n, dots);
+            if (tid == 0) {
+                for (int i = upd_n - 1; i >= 0; i--) dots[upd_list[i]] = dots[i];  // listed order -> RHS index
+                run_hook(HOOK_RELIABLE, &st, dots, n);
+            }
             __syncthreads();
             if (st.update[r] && st.active[r] && row_ok) {
                 const rp be = (rp)st.beta[r][0];

@@ -754,10 +754,10 @@ static int build_graph(const Solve &S) {
 // Persistent driver: the whole plain-CG solve of a bundle in one cooperative launch
 // ------------------------------------------------------------------------------------------
 // L2 residency of one link field during a persistent solve.  Every iteration reads the inner-
-// precision fat and Naik links once per Dslash, 182 times in a typical solve; the Naik copy (at
-// 32^3 x 8 with 16-bit storage, 75 MB of the 129 MB L2) is marked persisting through the stream's
-// access-policy window (hit ratio = the persisting set-aside / the window, so a larger field keeps
-// a random fraction of its lines), and only the other field and the vectors stream from HBM.  The
+// precision fat and Naik links once per Dslash, 182 times in a typical solve; when the Naik copy
+// fits the device's persisting set-aside whole (at 32^3 x 8 with 16-bit storage, 75 MB of the
+// 129 MB L2) it is marked persisting through the stream's access-policy window, and only the
+// other field and the vectors stream from HBM.  The
 // set-aside is reserved once per context (restored by hisq_finalize) and the persisting lines are
 // released after each solve, so no solve starts with links left in L2 by another.
 static bool l2_window_begin(hisq_ctx *ctx, cudaStream_t st, const hisq_links *links) {
@@ -774,6 +774,10 @@ static bool l2_window_begin(hisq_ctx *ctx, cudaStream_t st, const hisq_links *li
     }
     if (ctx->l2_persist_max <= 0 || ctx->l2_window_max <= 0) return false;
     const size_t bytes = (size_t)2 * links->W * ctx->geom.Vh * sizeof(uint4);
+    // only a field that fits the set-aside whole: a window of partial hits takes L2 from the
+    // vectors for little (48^3 x 12 FP32: 764 MB of Naik links against 85 MB made the solve 7%
+    // slower)
+    if (bytes > (size_t)ctx->l2_persist_max) return false;
     if (!ctx->l2_limit_saved) {
         size_t old = 0;
         if (cudaDeviceGetLimit(&old, cudaLimitPersistingL2CacheSize) != cudaSuccess) {

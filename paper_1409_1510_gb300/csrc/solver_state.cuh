@@ -214,12 +214,13 @@ __device__ __forceinline__ void run_hook(int hook, SolverState *st, const double
             const bool at_tol = gn <= tb * tb;
             const bool drop = (!st->inner_fp64) && gn < du * du;
             const bool last = st->iters[k] >= st->max_iter;
-            if (at_tol || drop || last) any = 1;
+            if (at_tol || drop || last) {
+                st->update[k] = 1;
+                any = 1;
+            }
         }
-        if (any) {  // bundle-wide, as in HOOK_DECIDE
-            for (int k = 0; k < n; k++)
-                if (st->active[k]) st->update[k] = 1;
-        }
+        // per right-hand side: the persistent kernel's FP64 passes run over only the right-hand
+        // sides that recompute, so a pass costs in proportion to them
         st->any_update = any;
         st->update_rounds += any;
         int act = 0;
