@@ -208,7 +208,7 @@ typedef struct {
                              other drivers, four barriers */
     double multishift_tol; /* hisq_cg_multishift with inner_prec != FP64: relative residual to
                              which the shared low-precision iteration runs before the per-shift
-                             FP64 refinement; 0 (default) = 1e-6 for FP32, 1e-4 for FP16/BF16 */
+                             FP64 refinement; 0 (default) = 1e-7 for FP32, 1e-4 for FP16/BF16 */
     int l2_persist_links; /* persistent driver: 1 (default) keeps the inner-precision Naik links
                              resident in L2 during the solve when they fit the device's persisting
                              set-aside (stream access-policy window over them, released after the

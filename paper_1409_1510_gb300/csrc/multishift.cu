@@ -579,7 +579,7 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     const double mass2_base = mass * mass + sigma_base;
     double tol_shared = tol;
     if (prec != HISQ_FP64)
-        tol_shared = std::max(tol, P0.multishift_tol > 0.0 ? P0.multishift_tol : (prec == HISQ_FP32 ? 1e-6 : 1e-4));
+        tol_shared = std::max(tol, P0.multishift_tol > 0.0 ? P0.multishift_tol : (prec == HISQ_FP32 ? 1e-7 : 1e-4));
     HISQ_CHECK(ms_workspace(ctx, nshift, prec));
     MsWork *w = ctx->ms;
     cudaStream_t st = ctx->stream;
