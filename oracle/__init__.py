@@ -51,6 +51,12 @@ def _bind(so):
     so.oracle_cg_multishift.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
     so.oracle_cg_multishift.restype = ctypes.c_int
+    so.oracle_splitmix64.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
+    so.oracle_splitmix64.restype = ctypes.c_ulonglong
+    so.oracle_z2_noise.argtypes = [_I4, ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_int, _D]
+    so.oracle_trace_inverse.argtypes = [_I4, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_double,
+                                        _D]
+    so.oracle_trace_inverse.restype = ctypes.c_double
     return so
 
 
@@ -203,6 +209,26 @@ class Oracle:
                                            _p(x), float(tol), int(max_iter),
                                            its.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(rel))
         return x, it, its, rel
+
+    def trace_inverse(self, mass: float, nnoise: int, seed: int, tol: float = 1e-10):
+        """Z2-noise estimate of Tr A^{-1} on the even sites: (mean, per-noise samples)."""
+        samples = np.empty(nnoise)
+        mean = self._so.oracle_trace_inverse(self._L, _p(self.X), _p(self.N), float(mass), int(nnoise),
+                                             seed & (2**64 - 1), float(tol), _p(samples))
+        return mean, samples
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """The i-th output (from 0) of the splitmix64 generator started from seed."""
+    return int(lib().oracle_splitmix64(seed & (2**64 - 1), i))
+
+
+def z2_noise(dims, seed: int, first: int, n: int):
+    """n Z2 noise vectors [n][V/2][3] (complex, real parts +-1) of stream seed, from vector first."""
+    vh = int(np.prod(dims)) // 2
+    out = np.empty((n, vh, 3), dtype=np.complex128)
+    lib().oracle_z2_noise(_I4(*dims), seed & (2**64 - 1), first, n, _p(out))
+    return out
 
 
 def adam_step(theta, grad, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):

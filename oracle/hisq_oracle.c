@@ -674,3 +674,55 @@ int oracle_cg_multishift(const int L[4], const double *X, const double *N, doubl
     free(r); free(p); free(Ap); free(ps); free(zeta); free(live);
     return result;
 }
+
+/*
+ * Z2 noise for the stochastic trace estimates of Eq. (2).  The generator is splitmix64 (Steele,
+ * Lea & Flood 2014): the state advances by gamma = 0x9E3779B97F4A7C15 per output and each output
+ * is the state passed through the published mixing function.  oracle_splitmix64(seed, i) is the
+ * i-th output (i = 0, 1, ...) of the generator started from `seed`.
+ */
+unsigned long long oracle_splitmix64(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* n noise vectors [n][V/2][3][2] on the even sites: vector k (k = first, first + 1, ...), colour
+ * component e = 3 s + c takes the real value -1 if the top bit of output (3 V/2) k + e of the
+ * generator is set, else +1; imaginary parts are 0. */
+void oracle_z2_noise(const int L[4], unsigned long long seed, unsigned long long first, int n, double *out) {
+    long Vh = volume(L) / 2, per = 3 * Vh;
+    for (int k = 0; k < n; k++)
+        for (long e = 0; e < per; e++) {
+            unsigned long long z = oracle_splitmix64(seed, (first + (unsigned long long)k) * (unsigned long long)per + e);
+            out[((long)k * per + e) * 2] = (z >> 63) ? -1.0 : 1.0;
+            out[((long)k * per + e) * 2 + 1] = 0.0;
+        }
+}
+
+/*
+ * Stochastic estimate of Tr A^{-1} over the even sites, Eq. (2) without derivative factors:
+ * (1/N) sum_k eta_k^dag A^{-1} eta_k with eta_k = noise vector k of `seed`, each A^{-1} eta_k from
+ * oracle_cg to tol.  samples[k] (may be NULL) receives Re eta_k^dag A^{-1} eta_k.  Returns the
+ * mean, or NaN if a solve missed tol.  (For the staggered matrix M = m + D of Eq. (3), whose even
+ * block of M^{-1} is m A^{-1} and whose odd block has the same trace, Tr M^{-1} = 2 m Tr A^{-1}.)
+ */
+double oracle_trace_inverse(const int L[4], const double *X, const double *N, double mass, int nnoise,
+                            unsigned long long seed, double tol, double *samples) {
+    long Vh = volume(L) / 2, n = Vh * 3;
+    double *eta = (double *)malloc(sizeof(double) * n * 2);
+    double *x = (double *)malloc(sizeof(double) * n * 2);
+    double sum = 0.0;
+    int ok = 1;
+    for (int k = 0; k < nnoise; k++) {
+        double rel;
+        oracle_z2_noise(L, seed, (unsigned long long)k, 1, eta);
+        if (oracle_cg(L, X, N, mass, eta, x, tol, 100000, &rel) < 0) ok = 0;
+        double v = dot(eta, x, n).re;
+        if (samples) samples[k] = v;
+        sum += v;
+    }
+    free(eta); free(x);
+    return ok ? sum / nnoise : NAN;
+}

@@ -243,6 +243,39 @@ def pin_multishift_free_field_exact(make, dims=(8, 8, 8, 8), mass=0.05, tol=1e-1
     return it > 0 and max(errs) <= 1e-8, f"iters {it} {list(its)}, rel errs {max(errs):.2e}"
 
 
+def pin_trace_z2_unbiased(make, dims=(4, 4, 4, 6), mass=0.2, nnoise=96, seed=11, tol=1e-10):
+    """Eq. (2) without derivative factors: the Z2-noise estimate of Tr A^{-1} lies within four
+    standard errors of the exact trace of the dense inverse, where the error is the exact
+    standard deviation of a real-Z2 estimate of a Hermitian B = A^{-1},
+    sqrt(2 sum_{i != j} (Re B_ij)^2 / N); and its noise is +-1 with both signs present."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    mean, samples = o.trace_inverse(mass, nnoise, seed, tol)
+    B = np.linalg.inv(dense.a_matrix(dims, X, N, mass).toarray())
+    exact = float(np.trace(B).real)
+    off = B.real - np.diag(np.diag(B.real))
+    sigma = float(np.sqrt(2.0 * np.sum(off ** 2) / nnoise))
+    ok = np.isfinite(mean) and abs(mean - exact) <= 4.0 * sigma
+    return bool(ok), f"estimate {mean:.6f} exact {exact:.6f} sigma {sigma:.2e}"
+
+
+def pin_condensate_identity(make, dims=(4, 4, 4, 6), mass=0.3):
+    """Tr M^{-1} of the staggered matrix M = m + D (D assembled from Eq. (3), both parities)
+    equals 2 m Tr A^{-1} (A from the oracle, column by column); this ties the even-site trace the
+    estimator targets to the full fermion matrix."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    n = lat.half_volume * 3
+    eye = np.eye(n, dtype=np.complex128).reshape(n, lat.half_volume, 3)
+    A = o.aop(eye, mass).reshape(n, n).T
+    D = dense.dslash_matrix(dims, X, N).toarray()
+    M = mass * np.eye(D.shape[0]) + D
+    full = np.trace(np.linalg.inv(M))
+    half = 2.0 * mass * np.trace(np.linalg.inv(A))
+    err = abs(full - half) / abs(full)
+    return err <= 1e-11, f"Tr M^-1 {full:.8f}, 2 m Tr A^-1 {half:.8f}, rel {err:.1e}"
+
+
 def network_weights_identity():
     """Weights with only the identity path of channel 0 set: the network is the identity."""
     W1 = np.zeros((17, 4, 1), complex); W1[0, 0, 0] = 1
@@ -389,7 +422,7 @@ def pin_network_normal_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=16, tol=1e-
 ALL_PINS = [
     pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
     pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
-    pin_multishift_dense_solve, pin_multishift_free_field_exact,
+    pin_multishift_dense_solve, pin_multishift_free_field_exact, pin_trace_z2_unbiased, pin_condensate_identity,
     pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd, pin_network_loss_zero_at_inverse,
     pin_fcg_identity_is_cg, pin_network_adjoint, pin_network_normal_gradient_fd,
 ]

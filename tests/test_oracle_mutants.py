@@ -1,7 +1,7 @@
 """Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the pins catch
 every one of them: a dropped term, a wrong sign, a wrong hop length or site, a transposed
 operand, a wrong mass term and a wrong CG coefficient, a missing conjugation in the adjoint
-network, a dropped term of the normal-form gradient, wrong multi-shift recurrences."""
+network, a dropped term of the normal-form gradient, wrong multi-shift recurrences, a wrong trace estimator or biased noise."""
 import os
 import tempfile
 
@@ -36,6 +36,8 @@ MUTANTS = {
     "multishift_beta_not_squared": ("double beta_j = beta_base * ratio * ratio;", "double beta_j = beta_base * ratio;"),
     "multishift_alpha_ratio_inverted": ("double alpha_j = alpha * zeta_new[j] / zeta[j];",
                                         "double alpha_j = alpha * zeta[j] / zeta_new[j];"),
+    "trace_estimator_uses_x_not_eta": ("double v = dot(eta, x, n).re;", "double v = dot(x, x, n).re;"),
+    "noise_not_symmetric": ("(z >> 63) ? -1.0 : 1.0", "(z >> 62) ? -1.0 : 1.0"),
     "normal_loss_missing_n_dag_term": ("oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */",
                                        "/* dropped */"),
 }

@@ -72,3 +72,29 @@ def test_adam_closed_form():
     for t in range(1, 6):
         oracle.adam_step(theta, g, m, v, t, lr, 0.9, 0.999, eps)
     np.testing.assert_allclose(theta, start - 5 * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12)
+
+
+def test_splitmix64_published_outputs():
+    """The noise generator reproduces the published first outputs of splitmix64 from seed 0."""
+    rows = []
+    with open(os.path.join(HERE, "golden", "splitmix64_seed0.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                i, h = line.split()
+                rows.append((int(i), int(h, 16)))
+    assert rows and all(oracle.splitmix64(0, i) == v for i, v in rows)
+
+
+def test_z2_noise_signs_follow_the_generator():
+    """Noise vector k, component e = 3 s + c is -1 exactly when the top bit of generator output
+    (3 V/2) k + e is set; both signs occur in balance."""
+    dims, seed = (4, 4, 4, 6), 5
+    eta = oracle.z2_noise(dims, seed, 2, 3)
+    per = eta.shape[1] * 3
+    flat = eta.reshape(3, -1)
+    for k in range(3):
+        for e in (0, 1, per // 2, per - 1):
+            top = oracle.splitmix64(seed, (2 + k) * per + e) >> 63
+            assert flat[k, e] == (-1.0 if top else 1.0)
+    assert np.all(eta.imag == 0) and np.all(np.abs(eta.real) == 1.0)
+    assert abs(eta.real.mean()) < 0.1
