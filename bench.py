@@ -44,12 +44,13 @@ def parse():
     ap.add_argument("--mass", type=float, default=DEFAULT_MASS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="cg",
-                    choices=["cg", "sweep", "learned", "batch", "production", "multishift"],
+                    choices=["cg", "sweep", "learned", "batch", "production", "multishift", "trace"],
                     help="cg: the benchmark line; sweep: Dslash throughput against the number of "
                          "right-hand sides; learned: the learned-preconditioner workload (32^3 x 8); "
                          "batch: bundles with uneven convergence (48^3 x 12); production: a sweep of "
                          "Z2-noise right-hand sides (64^3 x 16); multishift: eight shifted systems "
-                         "from one multi-shift solve against separate solves (32^3 x 8)")
+                         "from one multi-shift solve against separate solves (32^3 x 8); trace: the "
+                         "stochastic Tr A^-1 of Eq. (2) from Z2 noise (32^3 x 8)")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--test-rhs", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
@@ -920,8 +921,52 @@ def run_multishift(args):
     hisq.hisq_finalize()
 
 
+def run_trace(args):
+    """Eq. (2) without derivative factors on 32^3 x 8, m = 0.01: Tr A^{-1} over the even sites from
+    --nrhs Z2 noise vectors (default 64), FP16 storage with FP64 reliable updates, bundles chosen
+    by the autotuner, every solve to the FP64 true residual 1e-10; reports the estimate, its
+    standard error, Tr M^{-1} / V = 2 m Tr A^{-1} / V for M = m + D, and the time per noise vector."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims = tuple(int(x) for x in args.dims.split(","))
+    mass = args.mass
+    nnoise = args.nrhs if args.nrhs != 1500 else 64
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    hisq.hisq_init(dims, 0, torch.cuda.current_stream())
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    prec = PREC[args.inner]
+    fat = hisq.hisq_links_create(d64(X), False, prec, 18)
+    naik = hisq.hisq_links_create(d64(N), True, prec, 18)
+    p = hisq.hisq_default_solver_params()
+    p.inner_prec = prec
+    hisq.hisq_set_solver_params(p)
+    hisq.hisq_trace_inverse(fat, naik, mass, 16, 1, TOL)  # warm-up: tuning, first launches
+    samples = np.zeros(nnoise)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    est, err, _ = hisq.hisq_trace_inverse(fat, naik, mass, nnoise, 2026, TOL, samples)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    res = np.zeros(nnoise)
+    st = hisq.hisq_last_stats(None, res)
+    V = int(np.prod(dims))
+    line = {"mode": "trace", "lattice": list(dims), "mass": mass, "storage": args.inner, "nnoise": nnoise,
+            "seconds": sec, "s_per_noise": sec / nnoise, "trace_A_inv": est, "std_error": err,
+            "condensate_TrMinv_over_V": 2 * mass * est / V, "condensate_error": 2 * mass * err / V,
+            "bundle": int(st.bundle_size), "mean_iterations": st.total_iterations / nnoise,
+            "converged": int(st.converged), "max_true_residual": float(res.max())}
+    print(json.dumps(line), flush=True)
+    hisq.hisq_finalize()
+
+
 def main():
     args = parse()
+    if args.mode == "trace":
+        run_trace(args)
+        return
     if args.mode == "multishift":
         run_multishift(args)
         return

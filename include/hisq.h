@@ -244,6 +244,28 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
 int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik, const double *rhs, double *x[],
                        int nshift, const double *shifts, double mass, double tol);
 
+/* ---- stochastic traces (Eq. (2)) ----------------------------------------------------------- */
+
+/* Z2 noise vectors for the stochastic trace estimates of Eq. (2): out (device, canonical
+ * double[n][V/2][3][2]) receives vectors first .. first + n - 1 of the stream `seed`.  Component
+ * e = 3 s + c of vector k is -1 if the top bit of output (3 V/2) k + e of splitmix64 started from
+ * seed is set, else +1 (imaginary parts 0); splitmix64 (Steele, Lea & Flood 2014): state + i
+ * times 0x9E3779B97F4A7C15, then its mixing function, so every vector is generated independently
+ * on the device. */
+int hisq_z2_noise(double *out, int n, unsigned long long seed, unsigned long long first);
+
+/* Stochastic estimate of Tr A^{-1} over the even sites (Eq. (2) with no derivative factors):
+ * (1/N) sum_k Re eta_k^dag A^{-1} eta_k over the N = nnoise noise vectors 0 .. N-1 of `seed`
+ * (hisq_z2_noise), each solve by hisq_cg_solve's solver with the current parameters (precision,
+ * bundles) to tol, the products eta^dag x in FP64.  estimate, std_error (sample standard deviation
+ * over sqrt(N), 0 for N = 1; may be NULL) and samples (double[N], the per-noise products; may be
+ * NULL): host.  For the staggered matrix M = m + D, Tr M^{-1} = 2 m Tr A^{-1}.  hisq_last_stats
+ * then reports the solves (one entry per noise vector).  Allocates two chunks of up to 64
+ * canonical vectors for the duration of the call.  Errors as hisq_cg_solve. */
+int hisq_trace_inverse(const hisq_links *fat, const hisq_links *naik, double mass, int nnoise,
+                       unsigned long long seed, double tol, double *estimate, double *std_error,
+                       double *samples);
+
 typedef struct {
     int nrhs;
     int converged;            /* right-hand sides that met tol */

@@ -79,6 +79,8 @@ _SIGNATURES = {
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_cg_solve": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _D, _D], _I),
     "hisq_cg_multishift": ([_VP, _VP, _VP, ctypes.POINTER(_VP), _I, ctypes.POINTER(_D), _D, _D], _I),
+    "hisq_z2_noise": ([_VP, _I, ctypes.c_ulonglong, ctypes.c_ulonglong], _I),
+    "hisq_trace_inverse": ([_VP, _VP, _D, _I, ctypes.c_ulonglong, _D, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP], _I),
     "hisq_last_stats": ([ctypes.POINTER(hisq_solve_stats), _VP, _VP], _I),
     "hisq_autotune": ([_VP, _VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "hisq_set_launch_shape": ([_I, _I, _I, _I, _I, _I], _I),
@@ -236,6 +238,21 @@ def hisq_cg_multishift(fat, naik, rhs, x, shifts, mass: float, tol: float, raise
     if raise_on_error:
         _check(rc)
     return rc
+
+
+def hisq_z2_noise(out, n: int, seed: int, first: int = 0):
+    _check(load().hisq_z2_noise(_ptr(out), int(n), int(seed) & (2**64 - 1), int(first)))
+
+
+def hisq_trace_inverse(fat, naik, mass: float, nnoise: int, seed: int, tol: float, samples=None,
+                       raise_on_error: bool = True):
+    """Returns (estimate of Tr A^{-1}, its standard error, status); samples: host float64[nnoise] or None."""
+    est, err = _D(), _D()
+    rc = load().hisq_trace_inverse(fat, naik, float(mass), int(nnoise), int(seed) & (2**64 - 1), float(tol),
+                                   ctypes.byref(est), ctypes.byref(err), _ptr(samples))
+    if raise_on_error:
+        _check(rc)
+    return est.value, err.value, rc
 
 
 def hisq_last_stats(iterations=None, true_residual=None) -> hisq_solve_stats:
