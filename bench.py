@@ -185,8 +185,10 @@ def oracle_sample(lat, o, b, mass, budget_s):
     per_iter = time.perf_counter() - t
     iters = max(1, min(500, int(budget_s / max(per_iter, 1e-6))))
     t = time.perf_counter()
-    o.cg(b, mass, TOL, max_iter=iters)
+    _, done, _ = o.cg(b, mass, TOL, max_iter=iters)
     el = time.perf_counter() - t
+    if done > 0:  # converged before the budget: count the iterations it ran
+        iters = done
     flops = (2 * 1146 + 72) * lat.half_volume * iters
     return flops / el / 1e9, iters, el
 
@@ -226,6 +228,19 @@ def run_reference(args, rank):
             "e2e": {"value": value, "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+
+
+def combine_ranks(dist, total_ms, flops, launches, device):
+    """Whole-job figures of the timed region: the slowest rank's time, and the flops and kernel
+    launches summed over ranks (every rank solves its own right-hand side).  dist = None: one rank."""
+    if dist is None:
+        return total_ms, flops, launches
+    import torch
+    t = torch.tensor([total_ms, flops, launches], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), float(t[2])
 
 
 # ---------------------------------------------------------------------------------------------
@@ -310,14 +325,7 @@ def run_ours(args, rank, world, local_rank, dist):
     iters = stats[-1].max_iterations
     res = np.zeros(1)
     hisq.hisq_last_stats(None, res)
-    if dist is not None:
-        t = torch.tensor([total_ms, flops, launches], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, flops_all, launches_all = float(tmax[0]), float(t[1]), float(t[2])
-    else:
-        total_ms_max, flops_all, launches_all = total_ms, flops, launches
+    total_ms_max, flops_all, launches_all = combine_ranks(dist, total_ms, flops, launches, dev)
     value = flops_all / (total_ms_max / 1e3) / 1e9
 
     # the same solve driven by the captured CUDA graph, for comparison
