@@ -654,7 +654,7 @@ def run_learned(args):
                               rounds=6)
     t_train = time.perf_counter() - t0
     # fresh right-hand sides: plain CG against flexible CG with the network (both FP32 inner,
-    # FP64 reliable updates, true residual 1e-10 judged in FP64)
+    # FP64 reliable updates, true residual 1e-10 checked in FP64)
     tests = [d64(hi.gaussian_rhs(lat, 9000 + k)) for k in range(args.test_rhs)]
     out = {}
     for name, handle in (("cg", None), ("fcg_learned", pc)):

@@ -1,4 +1,4 @@
-"""Multi-shift CG on the GPU through the C ABI.  Every shift is judged by the FP64 oracle's true
+"""Multi-shift CG on the GPU through the C ABI.  Every shift is checked by the FP64 oracle's true
 residual of its own system A + sigma_j = (m^2 + sigma_j) - D_eo D_oe, and the FP64 iteration also
 by the oracle's multi-shift iterates."""
 import math

@@ -1,4 +1,4 @@
-"""Mixed-precision, batched CG solves on the GPU through the C ABI; every solution is judged by the FP64
+"""Mixed-precision, batched CG solves on the GPU through the C ABI; every solution is checked by the FP64
 oracle's true residual |b - A x| / |b|."""
 import numpy as np
 import pytest
