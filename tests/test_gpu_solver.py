@@ -220,3 +220,19 @@ def test_graph_reused_after_persistent_solves():
             its.append(int(iters[0]))
         assert its[0] == its[2] == its[4]
         assert g.oracle.true_residual(b, x[0], 0.05)[0] <= TOL * SLACK
+
+
+def test_l2_resident_links_do_not_change_the_solve():
+    """With and without the persisting L2 window over the Naik links (32^3 x 8 FP16 fits the
+    set-aside): the same iterations and both at the FP64 true residual; repeated solves release
+    the window in between."""
+    dims = (32, 32, 32, 8)
+    with gpu(dims, 2) as g:
+        b = hi.gaussian_rhs(g.lat, 77)
+        runs = []
+        for l2 in (1, 0, 1):
+            x, stats, iters, res = _solve(g, [b], 0.01, inner_prec=2, l2_persist_links=l2)
+            assert res[0] <= TOL
+            runs.append(int(iters[0]))
+        assert max(runs) - min(runs) <= 1
+        assert g.oracle.true_residual(b, x[0], 0.01)[0] <= TOL * SLACK
