@@ -788,8 +788,10 @@ static bool l2_window_begin(hisq_ctx *ctx, cudaStream_t st, const hisq_links *li
         ctx->l2_limit_saved = true;
     }
     const size_t carve = std::min((size_t)ctx->l2_persist_max, bytes);
-    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, carve) != cudaSuccess) {
-        cudaGetLastError();
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) cudaGetLastError();
+    if (cur != carve && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, carve) != cudaSuccess) {
+        cudaGetLastError();  // the set-aside is reconfigured only when it changes
         return false;
     }
     cudaStreamAttrValue v;
