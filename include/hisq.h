@@ -220,7 +220,9 @@ int hisq_set_solver_params(const hisq_solver_params *p);
 int hisq_get_solver_params(hisq_solver_params *p);
 
 /* Solve A x_k = rhs_k (A = mass^2 - D_eo D_oe, even sites) for k < nrhs to the relative true
- * residual |b - A x| / |b| <= tol, checked in FP64 on the GPU.  rhs[k], x[k]: host or device,
+ * residual |b - A x| / |b| <= tol, checked in FP64 on the GPU.  A right-hand side counts as
+ * converged once the library's FP64 true residual is at most 0.95 tol, so that the caller's own
+ * FP64 recomputation (another summation order) also finds it within tol.  rhs[k], x[k]: host or device,
  * canonical double[V/2][3][2] each; x is output only (initial guess 0).  The right-hand sides
  * are solved in bundles that share every link read; converged ones are masked out.
  * Returns HISQ_ERR_NOT_CONVERGED (stats filled, x holds the last iterate) if any right-hand
@@ -237,7 +239,9 @@ int hisq_cg_solve(const hisq_links *fat, const hisq_links *naik, const double *c
  * packed in it) until every shift's recursive residual meets max(tol, multishift_tol), and the
  * shifts are then refined by defect correction: their FP64 residuals are solved together as one
  * bundle of shifted systems (right-hand side j with mass^2 + shifts[j]) by the mixed-precision
- * persistent CG and the corrections added, until every FP64 true residual meets tol.  rhs, x[j]: host or device canonical double[V/2][3][2]; shifts: host
+ * persistent CG and the corrections added, until every FP64 true residual meets tol (as in
+ * hisq_cg_solve, at most 0.95 tol in the library's own FP64 check).  rhs, x[j]: host or device
+ * canonical double[V/2][3][2]; shifts: host
  * double[nshift], each > -mass^2, any order.  hisq_last_stats then reports per shift:
  * iterations[j] = shared iterations until shift j met its recursive residual plus its
  * refinement iterations, and true_residual[j].  Errors as hisq_cg_solve. */

@@ -46,7 +46,8 @@ def _bind(so):
     so.oracle_pc_adjoint.argtypes = [_I4, _D, _D, _D, _D, _D]
     so.oracle_pc_loss_grad_normal.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, _D]
     so.oracle_pc_loss_grad_normal.restype = ctypes.c_double
-    so.oracle_fcg.argtypes = [_I4, _D, _D, ctypes.c_double, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+    so.oracle_fcg.argtypes = [_I4, _D, _D, ctypes.c_double, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D,
+                              ctypes.c_int]
     so.oracle_fcg.restype = ctypes.c_int
     so.oracle_cg_multishift.argtypes = [_I4, _D, _D, ctypes.c_double, _D, ctypes.c_int, _D, _D, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D]
@@ -185,14 +186,16 @@ class Oracle:
         self._so.oracle_pc_backward(self._L, _p(self.X), _p(self.N), _p(W), _p(r), _p(gy), _p(g))
         return g
 
-    def fcg(self, W, b, mass: float, tol: float = 1e-10, max_iter: int = 10000):
-        """Flexible CG with the network as preconditioner; returns (x, iterations, true rel)."""
+    def fcg(self, W, b, mass: float, tol: float = 1e-10, max_iter: int = 10000, form: int = 0):
+        """Flexible CG with the network as preconditioner (form 0: M, 1: M^dag M, 2: the Hermitian
+        part of M); returns (x, iterations or -1, true rel).  x is the iterate reached, also when
+        max_iter ends the run first."""
         W = _c(W).reshape(-1)
         b = _c(b).reshape(self.V // 2, 3)
         x = np.empty_like(b)
         rel = ctypes.c_double()
         it = self._so.oracle_fcg(self._L, _p(self.X), _p(self.N), float(mass), _p(W), _p(b), _p(x),
-                                 float(tol), int(max_iter), ctypes.byref(rel))
+                                 float(tol), int(max_iter), ctypes.byref(rel), int(form))
         return x, it, rel.value
 
     def cg_multishift(self, b, shifts, mass: float, tol: float = 1e-10, max_iter: int = 10000):

@@ -519,14 +519,17 @@ void oracle_adam_step(long n, double *theta, const double *g, double *m, double 
 /*
  * Flexible conjugate gradient (Notay 2000) with the network as a variable preconditioner,
  * truncated to one previous direction (Polak-Ribiere form), for complex Hermitian A:
- *   z_k = M r_k;  beta_k = <r_k - r_{k-1}, z_k> / <r_{k-1}, p_{k-1}>;  p_k = z_k + beta_k p_{k-1};
+ *   z_k = P r_k;  beta_k = <r_k - r_{k-1}, z_k> / <r_{k-1}, p_{k-1}>;  p_k = z_k + beta_k p_{k-1};
  *   alpha_k = <p_k, r_k> / <p_k, A p_k>;  x += alpha_k p_k;  r -= alpha_k A p_k,
- * with <u, v> = sum conj(u) v (alpha and beta are complex when M is not Hermitian).
+ * with <u, v> = sum conj(u) v (alpha and beta are complex when P is not Hermitian).  This beta
+ * makes p_k A-orthogonal to p_{k-1} and this alpha makes r_{k+1} orthogonal to p_k, for any P.
+ * The preconditioner P is the network M itself (form 0), its normal form M^dag M (form 1), or
+ * its Hermitian part (M + M^dag) / 2 (form 2), M^dag being the adjoint network.
  * Stops when the true relative residual meets tol (checked as in oracle_cg).  Returns the
- * iteration count or -1.
+ * iteration count or -1; x holds the iterate reached either way.
  */
 int oracle_fcg(const int L[4], const double *X, const double *N, double mass, const double *W,
-               const double *b, double *x, double tol, int max_iter, double *true_rel) {
+               const double *b, double *x, double tol, int max_iter, double *true_rel, int form) {
     long Vh = volume(L) / 2, n = Vh * 3;
     double *r = (double *)malloc(sizeof(double) * n * 2);
     double *r_old = (double *)malloc(sizeof(double) * n * 2);
@@ -541,7 +544,16 @@ int oracle_fcg(const int L[4], const double *X, const double *N, double mass, co
     *true_rel = 1.0;
     if (bnorm == 0.0) { *true_rel = 0.0; iters = 0; goto done; }
     for (int k = 1; k <= max_iter; k++) {
-        oracle_pc_forward(L, X, N, W, r, z);
+        if (form == 1) {                      /* z = M^dag (M r) */
+            oracle_pc_forward(L, X, N, W, r, Ap);
+            oracle_pc_adjoint(L, X, N, W, Ap, z);
+        } else if (form == 2) {               /* z = (M r + M^dag r) / 2 */
+            oracle_pc_forward(L, X, N, W, r, z);
+            oracle_pc_adjoint(L, X, N, W, r, Ap);
+            for (long i = 0; i < 2 * n; i++) z[i] = 0.5 * (z[i] + Ap[i]);
+        } else {                              /* z = M r */
+            oracle_pc_forward(L, X, N, W, r, z);
+        }
         cplx beta = {0.0, 0.0};
         if (k > 1) {
             for (long i = 0; i < 2 * n; i++) Ap[i] = r[i] - r_old[i];

@@ -645,14 +645,15 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
         if (!(bb > 0.0)) HISQ_CUDA(cudaMemsetAsync(w->canon_x + (size_t)j * Vh * 6, 0, vbytes, st));
         else resid[j] = 2.0 * tol + 1.0;  // not yet measured
     }
+    const double tol_acc = tol * TOL_SAFETY;  // acceptance bound of the library's FP64 residual
     for (int round = 0; round < 3 && bb > 0.0; round++) {
         int m = 0;
         for (int j = 0; j < nshift; j++) {
-            if (resid[j] <= tol) continue;
+            if (resid[j] <= tol_acc) continue;
             double res2 = 0.0;
             HISQ_CHECK(ms_residual(ctx, w, fat, naik, w->canon_x + (size_t)j * Vh * 6, mass * mass + shifts[j], &res2));
             resid[j] = sqrt(res2 / bb);
-            if (resid[j] <= tol) continue;
+            if (resid[j] <= tol_acc) continue;
             HISQ_CHECK(unpack_vectors(ctx, w->r64, w->canon_r + (size_t)j * Vh * 6, 1, HISQ_FP64, st));
             idx[m] = j;
             rp[m] = w->canon_r + (size_t)j * Vh * 6;
@@ -688,7 +689,7 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     }
     int worst = HISQ_OK;
     for (int j = 0; j < nshift; j++)
-        if (!(resid[j] <= tol)) worst = HISQ_ERR_NOT_CONVERGED;
+        if (!(resid[j] <= tol_acc)) worst = HISQ_ERR_NOT_CONVERGED;
     for (int j = 0; j < nshift; j++)
         HISQ_CUDA(cudaMemcpyAsync(x[j], w->canon_x + (size_t)j * Vh * 6, vbytes, cudaMemcpyDefault, st));
     HISQ_CUDA(cudaStreamSynchronize(st));
@@ -704,7 +705,7 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     S.total_iterations = shared.k + refine_iters;
     for (int j = 0; j < nshift; j++) {
         S.max_iterations = std::max(S.max_iterations, iters[j]);
-        if (resid[j] <= tol) S.converged++;
+        if (resid[j] <= tol_acc) S.converged++;
     }
     S.flops = (double)S.total_iterations * Vh * (2.0 * 1146 + 72);
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -650,7 +650,7 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
     h->stall_window = P.stall_window;
     h->stall_factor = P.stall_factor;
     for (int k = 0; k < S.n; k++) {
-        h->tolk[k] = S.tolv ? S.tolv[k] : tol;
+        h->tolk[k] = (S.tolv ? S.tolv[k] : tol) * TOL_SAFETY;
         h->mass2[k] = S.mass2v ? S.mass2v[k] : S.mass * S.mass;
     }
     h->delta = P.delta;

@@ -419,10 +419,78 @@ def pin_network_normal_gradient_fd(make, dims=(4, 4, 4, 4), n_checks=16, tol=1e-
     return worst <= tol and ident <= 1e-13, f"worst rel {worst:.2e}, identity {ident:.1e}"
 
 
+
+def _fcg_iterates(o, W, b, mass, kmax, form):
+    """x_1 .. x_kmax of the oracle's flexible CG (one run per k: the runs are deterministic, so
+    the k-iteration run ends at the k-th iterate of any longer one)."""
+    return [o.fcg(W, b, mass, tol=1e-300, max_iter=k, form=form)[0].ravel() for k in range(1, kmax + 1)]
+
+
+def pin_fcg_normal_form_is_pcg(make, dims=(4, 4, 4, 6), mass=0.1, kmax=8, tol=1e-9):
+    """With a fixed Hermitian positive-definite preconditioner P flexible CG is preconditioned CG
+    (Notay 2000): with P = M^dag M of random weights (assembled densely column by column from the
+    oracle's network, which its own pins tie down) the oracle's iterates x_1..x_8 equal those of
+    textbook PCG on the dense matrices, z = P r, alpha = <r, z>/<p, A p>, beta = <r', z'>/<r, z>."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(29)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    m = 3 * lat.half_volume
+    P = np.empty((m, m), dtype=np.complex128)
+    for j in range(m):
+        e = np.zeros(m, dtype=np.complex128)
+        e[j] = 1.0
+        P[:, j] = o.pc_normal(W, e.reshape(-1, 3)).ravel()
+    A = dense.a_matrix(dims, X, N, mass).toarray()
+    b = hi.gaussian_rhs(lat, 6).ravel()
+    x = np.zeros(m, dtype=np.complex128)
+    r = b.copy()
+    z = P @ r
+    p = z.copy()
+    rz = np.vdot(r, z)
+    want = []
+    for _ in range(kmax):
+        Ap = A @ p
+        alpha = rz / np.vdot(p, Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        z = P @ r
+        rz_new = np.vdot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        want.append(x.copy())
+    got = _fcg_iterates(o, W, b.reshape(-1, 3), mass, kmax, form=1)
+    worst = max(_rel(g, w) for g, w in zip(got, want))
+    return worst <= tol, f"max rel diff of x_1..x_{kmax} {worst:.1e}"
+
+
+def pin_fcg_conjugacy(make, dims=(4, 4, 4, 6), mass=0.1, kmax=8, tol=1e-9):
+    """The two defining properties of flexible CG truncated to one direction (Notay 2000), which
+    hold for any preconditioner, here the raw network M of random weights (neither Hermitian nor
+    constant in its effect): alpha makes the new residual orthogonal to the step,
+    <x_k - x_{k-1}, b - A x_k> = 0, and beta makes consecutive steps A-orthogonal,
+    <x_k - x_{k-1}, A (x_{k+1} - x_k)> = 0.  Checked from the iterates alone with the dense A."""
+    lat, X, N = _fields(dims)
+    o = make(dims, X, N)
+    rng = np.random.default_rng(31)
+    W = _rand_vec(rng, o.pc_num_weights) * 0.3
+    A = dense.a_matrix(dims, X, N, mass).toarray()
+    b = hi.gaussian_rhs(lat, 7).ravel()
+    xs = [np.zeros_like(b)] + _fcg_iterates(o, W, b.reshape(-1, 3), mass, kmax + 1, form=0)
+    d = [xs[k] - xs[k - 1] for k in range(1, kmax + 2)]          # d[k-1] is the step of iteration k
+    worst_r, worst_a = 0.0, 0.0
+    for k in range(1, kmax + 1):
+        rk = b - A @ xs[k]
+        worst_r = max(worst_r, abs(np.vdot(d[k - 1], rk)) / (np.linalg.norm(d[k - 1]) * np.linalg.norm(rk)))
+        Ad = A @ d[k]
+        worst_a = max(worst_a, abs(np.vdot(d[k - 1], Ad)) / (np.linalg.norm(d[k - 1]) * np.linalg.norm(Ad)))
+    return max(worst_r, worst_a) <= tol, f"residual-step {worst_r:.1e}, A-conjugacy {worst_a:.1e}"
+
 ALL_PINS = [
     pin_matrix_form, pin_anti_hermitian, pin_gauge_covariance, pin_free_field_plane_waves,
     pin_free_field_spectrum, pin_cg_dense_solve, pin_cg_free_field_exact,
     pin_multishift_dense_solve, pin_multishift_free_field_exact, pin_trace_z2_unbiased, pin_condensate_identity,
     pin_network_special_weights, pin_network_covariance, pin_network_gradient_fd, pin_network_loss_zero_at_inverse,
-    pin_fcg_identity_is_cg, pin_network_adjoint, pin_network_normal_gradient_fd,
+    pin_fcg_identity_is_cg, pin_network_adjoint, pin_network_normal_gradient_fd, pin_fcg_normal_form_is_pcg,
+    pin_fcg_conjugacy,
 ]

@@ -12,7 +12,7 @@ from gpu_util import PREC_TOL, gpu, rel_err
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-SLACK = 1.05
+SLACK = 1.0   # the library stops at 0.95 tol, so the oracle's own FP64 residual is within tol
 D48 = (48, 48, 48, 12)
 D64 = (64, 64, 64, 16)
 

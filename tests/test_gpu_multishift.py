@@ -12,7 +12,7 @@ from gpu_util import gpu
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-SLACK = 1.01
+SLACK = 1.0   # the library stops at 0.95 tol, so the oracle's own FP64 residual is within tol
 DIMS = (8, 10, 8, 6)
 MASS = 0.05                                    # m^2 = 0.0025
 SHIFTS = (0.003, 0.0, 0.05, -0.002, 1.0, 0.3)  # unsorted, one negative (> -m^2)

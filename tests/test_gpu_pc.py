@@ -186,13 +186,40 @@ def _fcg(g, pc, rhs, mass, graph=1, **kw):
 
 
 @pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("form", [1, 0])
+def test_fcg_iterates_match_oracle(graph, form):
+    """The GPU's flexible CG takes the oracle's steps: after k = 1..6 iterations with a fixed
+    random network (normal form M^dag M and Hermitian part of M) its iterate x_k equals the
+    oracle's, whose beta and alpha are pinned by preconditioned CG and by the A-orthogonality of
+    consecutive steps.  A wrong beta (Fletcher-Reeves numerator, misplaced conjugate) moves x_2 on
+    by far more than the FP32 storage and network arithmetic do."""
+    mass = 0.1
+    with gpu(DIMS, 1) as g:
+        W = _weights(7, 0.3)
+        pc = g.hisq.hisq_pc_create(_as_real(W))
+        g.hisq.hisq_pc_set_form(pc, form)
+        b = hi.gaussian_rhs(g.lat, 650)
+        worst = 0.0
+        for k in range(1, 7):
+            p = g.hisq.hisq_default_solver_params()
+            p.inner_prec, p.use_graph, p.pc, p.max_iter = 1, graph, pc.value, k
+            g.hisq.hisq_set_solver_params(p)
+            x = np.zeros_like(b)
+            rc = g.hisq.hisq_cg_solve(g.fat, g.naik, [b], [x], mass, TOL, raise_on_error=False)
+            assert rc in (0, -4)  # HISQ_OK or HISQ_ERR_NOT_CONVERGED (max_iter reached)
+            want, _, _ = g.oracle.fcg(W, b, mass, tol=1e-300, max_iter=k, form=2 if form == 0 else 1)
+            worst = max(worst, rel_err(x[None], want[None]))
+        assert worst <= 1e-4, worst
+
+
+@pytest.mark.parametrize("graph", [0, 1])
 def test_fcg_identity_network_is_cg(graph):
     mass = 0.05
     with gpu(DIMS, 1) as g:
         rhs = [hi.gaussian_rhs(g.lat, 300 + k) for k in range(2)]
         pc = g.hisq.hisq_pc_create(None)
         x, stats, iters = _fcg(g, pc, rhs, mass, graph)
-        assert np.all(g.oracle.true_residual(np.stack(rhs), x, mass) <= TOL * 1.01)
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x, mass) <= TOL)
         _, _, it_cg = _fcg(g, None, rhs, mass, graph)
         assert np.all(np.abs(iters - it_cg) <= 2), (iters, it_cg)
 
@@ -210,7 +237,7 @@ def test_fcg_with_trained_network_beats_plain_cg_in_iterations(graph, form):
         g.hisq.hisq_pc_train(pc, g.fat, g.naik, mass, rb, eb, len(r), 16, 60, 1e-2)
         rhs = [hi.gaussian_rhs(g.lat, 400 + k) for k in range(3)]
         x, stats, iters = _fcg(g, pc, rhs, mass, graph)
-        assert np.all(g.oracle.true_residual(np.stack(rhs), x, mass) <= TOL * 1.01)
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x, mass) <= TOL)
         _, _, it_cg = _fcg(g, None, rhs, mass, graph)
         assert np.mean(iters) < np.mean(it_cg), (iters, it_cg)
 
@@ -224,7 +251,7 @@ def test_fcg_stall_falls_back_to_cg():
         pc = g.hisq.hisq_pc_create(_as_real(pins.network_weights_aop(mass)))
         rhs = [hi.gaussian_rhs(g.lat, 500)]
         x, stats, iters = _fcg(g, pc, rhs, mass, 1, stall_window=5)
-        assert g.oracle.true_residual(rhs[0], x[0], mass)[0] <= TOL * 1.01
+        assert g.oracle.true_residual(rhs[0], x[0], mass)[0] <= TOL
         assert stats.fallbacks >= 1
 
 
@@ -307,4 +334,4 @@ def test_flexible_cg_graph_reused_after_a_persistent_plain_solve():
         _, s2, it2 = _fcg(g, None, rhs, mass, graph=2)
         x3, s3, it3 = _fcg(g, pc, rhs, mass, graph=1)
         assert s1.converged == s3.converged == 2 and np.array_equal(it1, it3)
-        assert np.all(g.oracle.true_residual(np.stack(rhs), x3, mass) <= TOL * 1.01)
+        assert np.all(g.oracle.true_residual(np.stack(rhs), x3, mass) <= TOL)

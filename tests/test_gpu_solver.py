@@ -9,7 +9,7 @@ from gpu_util import gpu
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-SLACK = 1.01   # the library checks the same FP64 residual; allow rounding-order differences
+SLACK = 1.0   # the library stops at 0.95 tol, so the oracle's own FP64 residual is within tol
 
 
 def _solve(g, rhs, mass, **params):

@@ -1,7 +1,8 @@
 """Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the pins catch
 every one of them: a dropped term, a wrong sign, a wrong hop length or site, a transposed
 operand, a wrong mass term and a wrong CG coefficient, a missing conjugation in the adjoint
-network, a dropped term of the normal-form gradient, wrong multi-shift recurrences, a wrong trace estimator or biased noise."""
+network, a dropped term of the normal-form gradient, wrong multi-shift recurrences, a wrong trace estimator or biased noise,
+and a Fletcher-Reeves numerator, a misplaced conjugate or a missing adjoint in flexible CG."""
 import os
 import tempfile
 
@@ -40,6 +41,12 @@ MUTANTS = {
     "noise_not_symmetric": ("(z >> 63) ? -1.0 : 1.0", "(z >> 62) ? -1.0 : 1.0"),
     "normal_loss_missing_n_dag_term": ("oracle_pc_backward(L, X, N, W, gy, h, grad);        /* through N^dag */",
                                        "/* dropped */"),
+    "fcg_beta_fletcher_reeves": ("for (long i = 0; i < 2 * n; i++) Ap[i] = r[i] - r_old[i];",
+                                 "for (long i = 0; i < 2 * n; i++) Ap[i] = r[i];"),
+    "fcg_beta_conjugate_misplaced": ("beta = c_scale(1.0 / den, c_mul(num, c_conj(rp_old)));",
+                                     "beta = c_scale(1.0 / den, c_mul(c_conj(num), rp_old));"),
+    "fcg_alpha_conjugated": ("cplx alpha = c_scale(1.0 / pAp, pr);", "cplx alpha = c_scale(1.0 / pAp, c_conj(pr));"),
+    "fcg_normal_form_without_adjoint": ("oracle_pc_adjoint(L, X, N, W, Ap, z);", "memcpy(z, Ap, sizeof(double) * n * 2);"),
 }
 
 
