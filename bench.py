@@ -44,18 +44,22 @@ def parse():
     ap.add_argument("--mass", type=float, default=DEFAULT_MASS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="cg",
-                    choices=["cg", "sweep", "learned", "batch", "production", "multishift", "trace"],
+                    choices=["cg", "sweep", "learned", "batch", "production", "multishift", "trace", "dslash"],
                     help="cg: the benchmark line; sweep: Dslash throughput against the number of "
                          "right-hand sides; learned: the learned-preconditioner workload (32^3 x 8); "
                          "batch: bundles with uneven convergence (48^3 x 12); production: a sweep of "
                          "Z2-noise right-hand sides (64^3 x 16); multishift: eight shifted systems "
                          "from one multi-shift solve against separate solves (32^3 x 8); trace: the "
-                         "stochastic Tr A^-1 of Eq. (2) from Z2 noise (32^3 x 8)")
+                         "stochastic Tr A^-1 of Eq. (2) from Z2 noise (32^3 x 8); dslash: one Dslash "
+                         "configuration (--inner, --nrhs, --dims) launched --steps times (for profiling)")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--test-rhs", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--nrhs", type=int, default=1500, help="production: right-hand sides in the sweep")
     ap.add_argument("--pc", action="store_true", help="production: also train and apply the network")
+    ap.add_argument("--shape", default=None,
+                    help="dslash: launch shape R,threads,lanes (skips the autotuner, so that the only "
+                         "Dslash launches are one warm-up and the --steps timed ones)")
     return ap.parse_args()
 
 
@@ -540,6 +544,56 @@ def run_sweep(args):
     hisq.hisq_finalize()
 
 
+def run_dslash(args):
+    """One Dslash configuration: links and --nrhs right-hand sides (default 16) in --inner
+    storage on --dims, launched --steps times with the L2 flushed before each (CUDA events);
+    prints the median time, GFlop/s and compulsory GB/s and the launch shape."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import accounting as acc
+    from paper_1409_1510_gb300 import hisq
+    dims, _ = workload(args)
+    n = args.nrhs if args.nrhs != 1500 else 16
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    hisq.hisq_init(dims, 0, stream)
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    prec = PREC[args.inner] if args.inner in PREC else 2
+    fat = hisq.hisq_links_create(d64(X), False, prec, 18)
+    naik = hisq.hisq_links_create(d64(N), True, prec, 18)
+    vin = torch.empty(hisq.hisq_vector_bytes(prec, n), dtype=torch.uint8, device=dev)
+    hisq.hisq_pack(d64(np.stack([hi.gaussian_rhs(lat, k) for k in range(n)])), vin, n, prec)
+    vout = torch.empty_like(vin)
+    if args.shape:
+        shape = tuple(int(v) for v in args.shape.split(","))
+        hisq.hisq_set_launch_shape(prec, 18, n, *shape)
+    else:
+        shape = hisq.hisq_autotune(fat, naik, n)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    hisq.hisq_dslash(fat, naik, vin, vout, n, 1)  # warm-up
+    ts = []
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hisq.hisq_dslash(fat, naik, vin, vout, n, i % 2)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    sec = statistics.median(ts) / 1e3
+    elem = {0: 8, 1: 4, 2: 2, 3: 2}[prec]
+    byts = acc.compulsory_bytes(n, elem, elem, 18, 8.0 if prec in (2, 3) else 0.0, 4.0 if prec == 2 else 0.0) \
+        * lat.half_volume
+    hbm_peak, _ = peaks()
+    print(json.dumps({"mode": "dslash", "lattice": dims, "precision": args.inner, "nrhs": n, "launches": args.steps,
+                      "us": sec * 1e6, "gflops": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e9,
+                      "gbs": byts / sec / 1e9, "frac_hbm": byts / sec / 1e9 / hbm_peak,
+                      "shape_arg": ",".join(str(v) for v in shape)}), flush=True)
+    hisq.hisq_finalize()
+
+
 def make_pairs(hisq, torch, hi, lat, fat, naik, mass, d64, want):
     """(r, e) training pairs from plain FP32 CG on this gauge field: 16 right-hand sides at a time
     are solved to 1e-10 (x*), then re-solved for k iterations (x_k) at 25 values of k up to 80% of
@@ -989,6 +1043,9 @@ def main():
         return
     if args.mode == "sweep":
         run_sweep(args)
+        return
+    if args.mode == "dslash":
+        run_dslash(args)
         return
     if args.mode == "learned":
         run_learned(args)

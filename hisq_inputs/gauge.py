@@ -25,6 +25,8 @@ The fields follow the synthetic recipe used throughout this project:
 """
 from __future__ import annotations
 
+import concurrent.futures
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -125,14 +127,29 @@ def _exp_i_traceless_hermitian(q: np.ndarray) -> np.ndarray:
     return out
 
 
+def _workers() -> int:
+    return max(1, min(8, os.cpu_count() or 1))
+
+
 def random_su3(rng: np.random.Generator, count: int, eps: float) -> np.ndarray:
-    """``count`` matrices exp(i*eps*H), H = sum_a h_a lambda_a/2 with h_a ~ N(0, 1)."""
+    """``count`` matrices exp(i*eps*H), H = sum_a h_a lambda_a/2 with h_a ~ N(0, 1).  The draws
+    come first, in order; the exponentials of fixed chunks then run on a few threads (numpy
+    releases the GIL), each matrix computed exactly as in a serial loop."""
     h = rng.standard_normal((count, 8))
     out = np.empty((count, 3, 3), np.complex128)
     chunk = 1 << 20
-    for i0 in range(0, count, chunk):
+
+    def one(i0):
         q = eps * np.einsum("na,aij->nij", h[i0:i0 + chunk], _GELL_MANN / 2)
         out[i0:i0 + chunk] = _exp_i_traceless_hermitian(q)
+
+    starts = range(0, count, chunk)
+    if len(starts) > 1:
+        with concurrent.futures.ThreadPoolExecutor(_workers()) as ex:
+            list(ex.map(one, starts))
+    else:
+        for i0 in starts:
+            one(i0)
     return out
 
 
@@ -176,12 +193,16 @@ def naik_links(lat: Lattice, eps: float = 0.3, seed_u: int = SEED_NAIK_U,
     v = lat.volume
     u = random_su3(np.random.default_rng(seed_u), 4 * v, eps).reshape(4, v, 3, 3)
     out = np.empty_like(u)
-    for mu in range(4):
+
+    def one(mu):
         axis = 3 - mu  # grid axes are (t, z, y, x) after the leading direction axis is dropped
         g = lat._grid(u[mu:mu + 1])[0]
         g1 = np.roll(g, -1, axis=axis)
         g2 = np.roll(g, -2, axis=axis)
         out[mu] = (g @ g1 @ g2).reshape(v, 3, 3)
+
+    with concurrent.futures.ThreadPoolExecutor(min(4, _workers())) as ex:
+        list(ex.map(one, range(4)))
     return _fold(lat, -out / 24.0, 3, antiperiodic_t)
 
 
