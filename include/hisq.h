@@ -146,6 +146,18 @@ int hisq_dslash_full(const hisq_links *fat, const hisq_links *naik, const void *
 int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,
              void *out, int nrhs, double *pAp);
 
+/* FP64-accurate residual r_k = rhs_k - A x_k, A = mass^2 - D_eo D_oe on the even sites (the
+ * operator of Sec. 1's inversions, Eq. (3) restricted to the two parities), for k < nrhs, in the
+ * arithmetic the solvers' reliable updates use for these links: for FP32/FP16/BF16 handles the
+ * double-single form of the links (every FP64 real as a pair of floats, 48-bit significand) with
+ * exact products (Dekker 1971, by fused multiply-add) and error-free sums (Knuth's two-sum,
+ * Ogita-Rump-Oishi cascaded summation) on the FP32 pipe, then b - m^2 x + D t in FP64; for FP64
+ * handles native FP64.  rhs, x, r: host or device canonical double[nrhs][V/2][3][2] (r may alias
+ * neither); res2: host or device double[nrhs] receiving |r_k|^2 (may be NULL).  Allocates its
+ * scratch (cudaMalloc) for the call and synchronises the context's stream. */
+int hisq_residual(const hisq_links *fat, const hisq_links *naik, double mass, const double *rhs,
+                  const double *x, double *r, int nrhs, double *res2);
+
 /* ---- A-operator without allocation -------------------------------------------------------- */
 
 /* Size of the static device scratch behind hisq_aop_noalloc (per device, held until exit). */
@@ -299,6 +311,8 @@ typedef struct {
     int shared_iterations;    /* hisq_cg_multishift: iterations of the shared multi-shift CG */
     long refine_iterations;   /* hisq_cg_multishift: CG iterations of the per-shift refinements */
     double shared_seconds;    /* hisq_cg_multishift: wall time of the shared iteration */
+    long recompute_passes;    /* bundle iterations that ran a residual recomputation (each pass
+                                 reads the FP64-accurate links once for the right-hand sides due) */
 } hisq_solve_stats;
 
 /* Statistics of the calling thread's last hisq_cg_solve or hisq_cg_multishift.  iterations

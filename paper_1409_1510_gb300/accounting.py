@@ -96,3 +96,26 @@ def multishift_iteration_bytes(prec: int, live_shifts: int) -> float:
     P = VECTOR_BYTES[prec]
     Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
     return 2 * LINK_BYTES_18[prec] + 8 * P + 3 * Q + 4 * Q * live_shifts
+
+
+def recompute_flops(half_volume: int, reliable_updates: int) -> float:
+    """Algorithmic flops of the residual recomputations: two Dslash (1146 flop per site and
+    right-hand side each) per recomputation of one right-hand side; the m^2 x and b terms are
+    counted with the iteration."""
+    return 2.0 * DSLASH_FLOPS_PER_SITE * half_volume * reliable_updates
+
+
+def bundle_solve_bytes(prec: int, half_volume: int, total_iterations: int, bundle_iterations: int,
+                       reliable_updates: int, recompute_passes: int, nrhs: int) -> float:
+    """Algorithmic bytes of the bundle solves of one hisq_cg_solve: the links once per bundle
+    iteration (both Dslash), the vectors of every right-hand side once per iteration it ran
+    (9 P + 5 Q), the FP64-accurate links (double-single or FP64: 8 bytes per real) once per
+    recomputation pass (both Dslash), the vectors of every recomputed right-hand side, and the
+    setup of every right-hand side."""
+    P = VECTOR_BYTES[prec]
+    Q = VECTOR_BYTES[0] if prec == 0 else VECTOR_BYTES[1]
+    L64 = LINK_BYTES_18[0]
+    per_rhs_recompute = (2 * Q + 96.0) + 96.0 + (144.0 + Q)
+    total = (bundle_iterations * 2 * LINK_BYTES_18[prec] + total_iterations * (9 * P + 5 * Q)
+             + recompute_passes * 2 * L64 + reliable_updates * per_rhs_recompute + nrhs * cg_setup_bytes(prec))
+    return total * half_volume

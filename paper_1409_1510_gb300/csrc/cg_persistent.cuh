@@ -13,16 +13,19 @@
 // (L2), never the read-only path.
 #pragma once
 #include "dslash_kernel.cuh"
+#include "ds_arith.cuh"
 
 namespace hisq {
 
 struct PersArgs {
     Geom g;
     LinkField fat, naik;      // inner precision (18-real Naik)
-    LinkField fat64, naik64;  // FP64 copies
+    LinkField fat64, naik64;  // FP64 links of the residual recomputation: the FP64 copies (P = FP64)
+                              // or the double-single copies (otherwise)
     void *p, *t, *ap;         // inner precision bundles
     void *x, *r;              // x_lo and r in the iterated precision
-    void *b, *xhi, *t64;      // FP64
+    void *b, *xhi, *t64;      // FP64 (t64: double-single when P != FP64)
+    void *xds;                // x_hi in double-single form (P != FP64)
     int n;
     double *partials;         // [gridDim][PERS_ND]
     SolverState *st;          // initial state in, final state out (block 0)
@@ -374,6 +377,66 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
         publish_dots_k<R, 2>(a, red, dot, t, gi, n, 2 * n);
     } else if constexpr (EPI != EPI_PLAIN) {
         publish_dots<R>(a, red, dot[0], t, gi, list ? nlist : n);  // with a list: column i = list[i]
+    }
+}
+
+// The FP64-accurate residual recomputation of a mixed-precision solve in double-single
+// arithmetic (ds_arith.cuh) over the block's share of the sites, one thread per (site, listed
+// right-hand side list[i], i < nlist).  EPI_PLAIN: out = D in (ds bundles).  EPI_RESID:
+// r = b - m^2 x + D in with x, b FP64 and an FP64 epilogue, written to out_lo in the iterated
+// precision Q, with |r|^2 per block published as column i of the list.
+template <int EPI, int Q>
+__device__ __forceinline__ void ds_phase(const PersArgs &a, const void *in, void *out, int parity, const void *xvec,
+                                         const void *bvec, void *out_lo, double *red, const double *m2v,
+                                         const int *list, int nlist) {
+    const Geom &g = a.g;
+    const int n = a.n, t = nlist, spb = blockDim.x / t;
+    const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = list[gi];
+    const bool act[1] = {true};
+    double dot[1] = {0.0};
+    const int ts = tile_sites(g.Vh, spb);
+    if (sl < ts) {
+        for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
+            const int s = tile * ts + sl;
+            if (s >= g.Vh) break;
+            dscplx acc[1][3];
+            ds_site_stencil<1, true>(g, a.fat64, a.naik64, parity, reinterpret_cast<const float4 *>(in), n, s, r0, act,
+                                     acc);
+            if constexpr (EPI == EPI_PLAIN) {
+                ds_store3(reinterpret_cast<float4 *>(out), n, s, r0, acc[0]);
+            } else {
+                static_assert(EPI == EPI_RESID, "the double-single phases are D in and the residual");
+                const double m2 = m2v[r0];
+                const double2 *vx = reinterpret_cast<const double2 *>(xvec);
+                const double2 *vb = reinterpret_cast<const double2 *>(bvec);
+                Cplx<typename Prec<Q>::real> lo3[3];
+                double d = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const long idx = ((long)s * 3 + c) * n + r0;
+                    const double2 x = __ldcg(vx + idx), b = __ldcg(vb + idx);
+                    const double wr = b.x - m2 * x.x + ds_value(acc[0][c].re);
+                    const double wi = b.y - m2 * x.y + ds_value(acc[0][c].im);
+                    d += wr * wr + wi * wi;
+                    lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+                }
+                dot[0] += d;
+                store_vec<Q>(VecView<Q>{out_lo, n}, s, r0, lo3);
+            }
+        }
+    }
+    if constexpr (EPI == EPI_RESID) publish_dots<1>(a, red, dot, t, gi, nlist);
+}
+
+// x_hi of one site and right-hand side, written in double-single form for the recomputation
+__device__ __forceinline__ void store_xds(const PersArgs &a, int s, int r, const Cplx<double> xh[3]) {
+    float4 *o = reinterpret_cast<float4 *>(a.xds);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float rh, rl, ih, il;
+        ds_split(xh[c].re, rh, rl);
+        ds_split(xh[c].im, ih, il);
+        o[((long)s * 3 + c) * a.n + r] = make_float4(rh, rl, ih, il);
     }
 }
 

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
 #pragma unroll
                     for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
                     store_vec<HISQ_FP64>(V64(xhi), s, r, xh);
+                    if constexpr (P != HISQ_FP64) store_xds(a, s, r, xh);
                     store_vec<Q>(VQ(x), s, r, zq);
                 } else {
 #pragma unroll
@@ -141,13 +142,19 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
                 upd_n = u;
             }
             __syncthreads();
-            dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
-                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red,
-                                                     st.mass2, upd_list, upd_n);
-            if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
-                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red,
-                                                     st.mass2, upd_list, upd_n);
+            if constexpr (P == HISQ_FP64) {
+                dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64,
+                                                         1, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr,
+                                                         nullptr, red, st.mass2, upd_list, upd_n);
+                if (!(ok = grid_sync(a))) break;
+                dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)},
+                                                         nullptr, 0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b,
+                                                         a.r, red, st.mass2, upd_list, upd_n);
+            } else {
+                ds_phase<EPI_PLAIN, Q>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
+                if (!(ok = grid_sync(a))) break;
+                ds_phase<EPI_RESID, Q>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
+            }
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, upd_n, dots);
             if (tid == 0) {
@@ -238,17 +245,40 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
 #pragma unroll
                     for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
                     store_vec<HISQ_FP64>(V64(xhi), s, r, xh);
+                    if constexpr (P != HISQ_FP64) store_xds(a, s, r, xh);
                     store_vec<Q>(VQ(x), s, r, zq);
                 }
             }
             if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64, 1,
-                                                     st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr, nullptr, red, st.mass2);
-            if (!(ok = grid_sync(a))) break;
-            dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)}, nullptr,
-                                                     0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b, a.r, red, st.mass2);
-            if (!(ok = grid_sync(a))) break;
-            sum_partials(a, red, n, dots);
+            if constexpr (P == HISQ_FP64) {
+                dslash_phase<HISQ_FP64, 1, EPI_PLAIN, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.t64,
+                                                         1, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, nullptr,
+                                                         nullptr, red, st.mass2);
+                if (!(ok = grid_sync(a))) break;
+                dslash_phase<HISQ_FP64, 1, EPI_RESID, Q>(a, a.fat64, a.naik64, PlainIn<HISQ_FP64, true>{V64(t64)},
+                                                         nullptr, 0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b,
+                                                         a.r, red, st.mass2);
+                if (!(ok = grid_sync(a))) break;
+                sum_partials(a, red, n, dots);
+            } else {
+                // the right-hand sides due for the recomputation, listed (this form recomputes
+                // bundle-wide, so every active one)
+                if (tid == 0) {
+                    int u = 0;
+                    for (int k = 0; k < n; k++)
+                        if (st.update[k]) upd_list[u++] = k;
+                    upd_n = u;
+                }
+                __syncthreads();
+                ds_phase<EPI_PLAIN, Q>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
+                if (!(ok = grid_sync(a))) break;
+                ds_phase<EPI_RESID, Q>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
+                if (!(ok = grid_sync(a))) break;
+                sum_partials(a, red, upd_n, dots);
+                if (tid == 0)
+                    for (int i = upd_n - 1; i >= 0; i--) dots[upd_list[i]] = dots[i];  // listed order -> RHS index
+                __syncthreads();
+            }
             if (tid == 0) run_hook(HOOK_RELIABLE, &st, dots, n);
             __syncthreads();
             clock_mark(clk, PH_RELIABLE);

@@ -99,12 +99,23 @@ __device__ inline void gathered_link(const Geom &g, const double *U, int s, int 
 }
 
 template <int P>
+__host__ __device__ constexpr int stored_real_bytes() {
+    if constexpr (P == HISQ_DS) return 8;  // the (hi, lo) float pair
+    else return Prec<P>::bytes;
+}
+
+template <int P>
 __device__ inline void put_real(uint4 *words, int Vh, int W, int parity, int s, int e, double val) {
-    constexpr int EB = Prec<P>::bytes;
+    constexpr int EB = stored_real_bytes<P>();
     int off = e * EB;
     int j = off / 16, b = off % 16;
     char *base = reinterpret_cast<char *>(words + ((size_t)parity * W + j) * Vh + s) + b;
     if constexpr (P == HISQ_FP64) *reinterpret_cast<double *>(base) = val;
+    else if constexpr (P == HISQ_DS) {
+        const float hi = __double2float_rn(val);
+        reinterpret_cast<float *>(base)[0] = hi;
+        reinterpret_cast<float *>(base)[1] = __double2float_rn(val - (double)hi);
+    }
     else if constexpr (P == HISQ_FP32) *reinterpret_cast<float *>(base) = (float)val;
     else if constexpr (P == HISQ_FP16) *reinterpret_cast<__half *>(base) = __double2half(val);
     else *reinterpret_cast<__nv_bfloat16 *>(base) = __double2bfloat16(val);
@@ -222,6 +233,7 @@ static void launch_export(int recon, const Geom &g, LinkField f, double *out, cu
 static void dispatch_pack(int prec, int recon, const Geom &g, const double *U, int hop, uint4 *words, float *scale,
                           int W, cudaStream_t st) {
     switch (prec) {
+    case HISQ_DS: launch_pack<HISQ_DS>(18, g, U, hop, words, scale, W, st); break;
     case HISQ_FP64: launch_pack<HISQ_FP64>(recon, g, U, hop, words, scale, W, st); break;
     case HISQ_FP32: launch_pack<HISQ_FP32>(recon, g, U, hop, words, scale, W, st); break;
     case HISQ_FP16: launch_pack<HISQ_FP16>(recon, g, U, hop, words, scale, W, st); break;
@@ -296,7 +308,7 @@ int unpack_vectors(hisq_ctx *ctx, const void *internal, double *canon_dev, int n
 LaunchShape default_shape(int prec, int n) {
     // right-hand sides per thread: largest of 4, 2, 1 dividing n (8 for FP64 is too many registers)
     int R = 1;
-    int maxR = prec == HISQ_FP64 ? 2 : 4;
+    int maxR = prec == HISQ_FP64 ? 2 : prec == HISQ_DS ? 1 : 4;
     for (int c = maxR; c >= 1; c /= 2)
         if (n % c == 0) { R = c; break; }
     return {R, 256, 1};
@@ -308,20 +320,26 @@ static int pow2_floor(int x) {
     return p;
 }
 
-int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, bool use64, const DslashArgs &d,
+int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int copy, const DslashArgs &d,
                   const LaunchShape *shape, cudaStream_t stream, int *grid_out) {
-    int prec = use64 ? HISQ_FP64 : fat->prec;
-    int recon = use64 ? 18 : naik->recon;
-    LaunchShape sh = shape ? *shape : tuned_shape(ctx, fat, naik, d.n, use64);
+    if (copy == LINKS_DS && !fat->residual_ds()) copy = LINKS_FP64;  // FP64 handles have no ds copy
+    if (copy == LINKS_DS && (!fat->words_ds || !naik->words_ds))
+        return set_error(HISQ_ERR_STATE, "links without their double-single copy");
+    const bool ds = copy == LINKS_DS;
+    int prec = copy_prec(fat, copy);
+    int recon = copy != LINKS_INNER ? 18 : naik->recon;
+    if (ds && d.epi == EPI_AOP) return set_error(HISQ_ERR_ARG, "double-single Dslash has no A-operator epilogue");
+    LaunchShape sh = shape ? *shape : tuned_shape(ctx, fat, naik, d.n, copy);
     int R = sh.R;
     if (R != 1 && R != 2 && R != 4 && R != 8) R = 1;
     if (d.n % R != 0) R = 1;
     if (prec == HISQ_FP64 && R > 4) R = 4;  // FP64 kernels are built for up to four RHS per thread
+    if (ds && R > 2) R = 2;                 // double-single kernels for up to two
     // lane splits exist for 18-real Naik records: two lanes up to four RHS per thread, four up to two
     int S = 1;
-    if (recon == 18 && sh.S == 2 && R <= 4) S = 2;
-    if (recon == 18 && sh.S == 4 && R <= 2) S = 4;
-    if (recon == 18 && sh.S == 8 && R <= 2 && prec != HISQ_FP64 && d.epi != EPI_RESID) S = 8;
+    if (!ds && recon == 18 && sh.S == 2 && R <= 4) S = 2;
+    if (!ds && recon == 18 && sh.S == 4 && R <= 2) S = 4;
+    if (!ds && recon == 18 && sh.S == 8 && R <= 2 && prec != HISQ_FP64 && d.epi != EPI_RESID) S = 8;
     int t = (d.n + R - 1) / R;
     // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
     // threads keep both the partial count and that block's share of the sum small
@@ -341,8 +359,8 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     KArgs a;
     memset(&a, 0, sizeof(a));
     a.g = ctx->geom;
-    a.fat = use64 ? fat->field64() : fat->field();
-    a.naik = use64 ? naik->field64() : naik->field();
+    a.fat = ds ? fat->field_ds() : copy == LINKS_FP64 ? fat->field64() : fat->field();
+    a.naik = ds ? naik->field_ds() : copy == LINKS_FP64 ? naik->field64() : naik->field();
     a.in = d.in;
     a.out = d.out;
     a.n = d.n;
@@ -383,6 +401,7 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int grid = 0;
     cudaError_t e;
     switch (prec) {
+    case HISQ_DS: e = launch_dslash_ds(a, d.epi, R, threads, smem, ctx->num_sms, stream, &grid); break;
     case HISQ_FP64: e = launch_dslash_prec<HISQ_FP64>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
     case HISQ_FP32: e = launch_dslash_prec<HISQ_FP32>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
     case HISQ_FP16: e = launch_dslash_prec<HISQ_FP16>(a, recon, d.epi, R, S, threads, smem, ctx->num_sms, stream, &grid); break;
@@ -512,6 +531,7 @@ int hisq_links_destroy(hisq_links *h) {
     if (h->words) cudaFree(h->words);
     if (h->scale) cudaFree(h->scale);
     if (h->words64) cudaFree(h->words64);
+    if (h->words_ds) cudaFree(h->words_ds);
     hisq_ctx *ctx = h->ctx;
     if (ctx) {
         ctx->links.erase(std::remove(ctx->links.begin(), ctx->links.end(), h), ctx->links.end());
@@ -586,10 +606,17 @@ int hisq_links_create(hisq_links **out, const double *canon, int is_naik, int pr
         rc = set_error(HISQ_ERR_NOMEM, "cannot allocate link scales");
     if (rc == HISQ_OK) dispatch_pack(prec, recon, g, U, hop, h->words, h->scale, h->W, st);
     if (rc == HISQ_OK && prec != HISQ_FP64) {
+        // the FP64 copy (plain FP64 solves with these links) and the double-single copy (the
+        // residual recomputations of mixed-precision solves)
         int W64 = link_words(HISQ_FP64, 18);
         size_t b64 = (size_t)2 * W64 * g.Vh * sizeof(uint4);
         if (cudaMalloc(&h->words64, b64) != cudaSuccess) rc = set_error(HISQ_ERR_NOMEM, "cannot allocate FP64 link copy");
         else dispatch_pack(HISQ_FP64, 18, g, U, hop, h->words64, nullptr, W64, st);
+        if (rc == HISQ_OK) {
+            if (cudaMalloc(&h->words_ds, b64) != cudaSuccess)
+                rc = set_error(HISQ_ERR_NOMEM, "cannot allocate double-single link copy");
+            else dispatch_pack(HISQ_DS, 18, g, U, hop, h->words_ds, nullptr, W64, st);
+        }
     }
     if (rc == HISQ_OK) {
         cudaError_t e = cudaGetLastError();

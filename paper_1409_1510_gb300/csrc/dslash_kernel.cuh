@@ -151,20 +151,6 @@ __device__ __forceinline__ void block_reduce_finish(double *red, int rows, int n
     }
 }
 
-// Neighbour `step` hops away along a direction mu known only at run time (the four-lane split
-// picks its directions by lane): the coordinate, extent and stride are selected, not indexed,
-// so nothing spills to local memory.
-__device__ __forceinline__ int neighbour_rt(const Geom &g, const SiteCoord &sc, int s, int mu, int step) {
-    const int cm = mu == 0 ? sc.c[0] : mu == 1 ? sc.c[1] : mu == 2 ? sc.c[2] : sc.c[3];
-    const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
-    const int st = mu == 1 ? g.stride[1] : mu == 2 ? g.stride[2] : g.stride[3];
-    int c = cm + step;
-    c += (c < 0) ? L : 0;
-    c -= (c >= L) ? L : 0;
-    if (mu == 0) return sc.row_base + (c >> 1);
-    return s + (c - cm) * st;
-}
-
 // The R neighbour vectors of the active right-hand sides (zeros for the inactive ones).
 template <int P, int R, bool COHERENT>
 __device__ __forceinline__ void load_neighbours(const VecView<P> &vin, int nb, int r0, const bool act[R],

@@ -94,5 +94,8 @@ inline cudaError_t launch_epi(const KArgs &a, int epi, int R, int S, int threads
 template <int P>
 cudaError_t launch_dslash_prec(const KArgs &a, int recon, int epi, int R, int S, int threads, size_t smem,
                                int num_sms, cudaStream_t s, int *grid);
+// The double-single entry (dslash_ds.cu): EPI_PLAIN or EPI_RESID, one or two RHS per thread.
+cudaError_t launch_dslash_ds(const KArgs &a, int epi, int R, int threads, size_t smem, int num_sms, cudaStream_t s,
+                             int *grid);
 
 }  // namespace hisq

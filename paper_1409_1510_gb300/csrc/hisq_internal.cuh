@@ -74,6 +74,20 @@ __host__ __device__ __forceinline__ int neighbour(const Geom &g, const SiteCoord
     return s + (c - sc.c[mu]) * g.stride[mu];
 }
 
+// Neighbour `step` hops away along a direction mu known only at run time (the four-lane split
+// picks its directions by lane; loops over the links that are not unrolled): the coordinate,
+// extent and stride are selected, not indexed, so nothing spills to local memory.
+__device__ __forceinline__ int neighbour_rt(const Geom &g, const SiteCoord &sc, int s, int mu, int step) {
+    const int cm = mu == 0 ? sc.c[0] : mu == 1 ? sc.c[1] : mu == 2 ? sc.c[2] : sc.c[3];
+    const int L = mu == 0 ? g.L[0] : mu == 1 ? g.L[1] : mu == 2 ? g.L[2] : g.L[3];
+    const int st = mu == 1 ? g.stride[1] : mu == 2 ? g.stride[2] : g.stride[3];
+    int c = cm + step;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    if (mu == 0) return sc.row_base + (c >> 1);
+    return s + (c - cm) * st;
+}
+
 // ------------------------------------------------------------------------------------------
 // Storage precisions
 // ------------------------------------------------------------------------------------------
@@ -85,6 +99,10 @@ template <> struct Prec<HISQ_BF16> { using real = float; using store = __nv_bflo
 
 template <typename R> struct Cplx { R re, im; };
 
+// Internal storage id of the double-single form of FP64 data (ds_arith.cuh): every real as the
+// float pair (hi, lo), 8 bytes, in the FP64 layouts.  Not a precision of the C ABI.
+constexpr int HISQ_DS = 4;
+
 // Internal vector bundles of n right-hand sides.  FP64, FP32 and BF16: element (s, c, r) is the
 // complex number at (s*3 + c)*n + r (double2 / float2 / bf16x2).  FP16: one 16-byte record per
 // (site, rhs) at s*n + r holding the three colour components as half2 and the FP32 scale
@@ -92,7 +110,8 @@ template <typename R> struct Cplx { R re, im; };
 inline size_t vector_bytes(int prec, int Vh, int n) {
     const size_t elems = (size_t)Vh * n;
     switch (prec) {
-    case HISQ_FP64: return elems * 3 * 16;
+    case HISQ_FP64:
+    case HISQ_DS: return elems * 3 * 16;
     case HISQ_FP32: return elems * 3 * 8;
     case HISQ_FP16: return elems * 16;
     default: return elems * 3 * 4;
@@ -231,7 +250,7 @@ struct LinkField {
 };
 
 __host__ __device__ constexpr int link_words(int prec, int recon) {
-    return 8 * recon * (prec == HISQ_FP64 ? 8 : prec == HISQ_FP32 ? 4 : 2) / 16;
+    return 8 * recon * ((prec == HISQ_FP64 || prec == HISQ_DS) ? 8 : prec == HISQ_FP32 ? 4 : 2) / 16;
 }
 
 }  // namespace hisq
@@ -248,11 +267,16 @@ struct hisq_links {
     uint4 *words;          // [2][W][Vh] main copy
     float *scale;          // [2][Vh] or null
     uint4 *words64;        // FP64 recon-18 copy (null when prec == FP64: use words)
+    uint4 *words_ds;       // double-single recon-18 copy (null when prec == FP64)
     hisq::LinkField field() const { return {words, scale, W}; }
     hisq::LinkField field64() const {
         if (prec == HISQ_FP64 && recon == 18) return {words, nullptr, W};
         return {words64, nullptr, hisq::link_words(HISQ_FP64, 18)};
     }
+    hisq::LinkField field_ds() const { return {words_ds, nullptr, hisq::link_words(hisq::HISQ_DS, 18)}; }
+    // the residual recomputation of a mixed-precision solve runs in double-single arithmetic on
+    // the FP32 pipe; FP64 handles keep native FP64 throughout
+    bool residual_ds() const { return prec != HISQ_FP64; }
 };
 
 struct hisq_pc {
@@ -365,12 +389,24 @@ struct DslashArgs {
     void *hook_state;
     int partials_only;     // reducing epilogues: publish per-block partials only (no finish)
 };
+// Which copy of the links a Dslash reads, and in which arithmetic: the handle's own storage
+// precision; the FP64 copy in FP64; or the double-single copy in double-single arithmetic (input
+// and, for EPI_PLAIN, output bundles in the ds form; EPI_RESID keeps x, b and r in FP64).
+enum LinkCopy { LINKS_INNER = 0, LINKS_FP64 = 1, LINKS_DS = 2 };
+// the copy that gives FP64 accuracy for these links: double-single unless they are FP64 already
+inline int links_hp(const hisq_links *fat) { return fat->residual_ds() ? LINKS_DS : LINKS_FP64; }
 // grid_out (optional) receives the number of blocks launched (= partials written per dot)
-int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, bool use64,
+int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int copy,
                   const DslashArgs &a, const LaunchShape *shape, cudaStream_t stream, int *grid_out = nullptr);
 LaunchShape default_shape(int prec, int n);
-LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64);
-int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64);  // tune.cu
+LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, int copy);
+int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, int copy);  // tune.cu
+// the precision id a copy computes in (tuning keys, vector sizes)
+inline int copy_prec(const hisq_links *fat, int copy) {
+    return copy == LINKS_DS ? HISQ_DS : copy == LINKS_FP64 ? HISQ_FP64 : fat->prec;
+}
+// FP64 bundle -> double-single bundle of n right-hand sides (dslash_ds.cu)
+int split_vectors(hisq_ctx *ctx, const void *fp64_bundle, void *ds_bundle, int n, cudaStream_t st);
 void free_workspace(hisq_ctx *ctx);  // solver.cu
 void free_multishift(hisq_ctx *ctx); // multishift.cu
 // CG solve of nrhs right-hand sides (solver.cu): hisq_cg_solve when mass2v and tolv are null;

@@ -284,6 +284,7 @@ struct MsWork {
     int prec = -1, cap = 0;
     void *b64 = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *ap = nullptr, *xs = nullptr, *ps = nullptr;
     void *x64 = nullptr, *t64 = nullptr, *r64 = nullptr;
+    void *x_ds = nullptr;  // x64 in double-single form (residual Dslash input for low-precision links)
     double *canon_b = nullptr, *canon_r = nullptr, *canon_e = nullptr, *canon_x = nullptr;  // canonical staging
     double *partials = nullptr;
     size_t partials_cap = 0;
@@ -309,11 +310,11 @@ static void ms_free_graph(MsWork *w) {
 }
 
 static void ms_free_buffers(MsWork *w) {
-    void *bufs[] = {w->b64, w->r, w->p, w->t, w->ap, w->xs, w->ps, w->x64, w->t64, w->r64,
+    void *bufs[] = {w->b64, w->r, w->p, w->t, w->ap, w->xs, w->ps, w->x64, w->t64, w->r64, w->x_ds,
                     w->canon_b, w->canon_r, w->canon_e, w->canon_x};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    w->b64 = w->r = w->p = w->t = w->ap = w->xs = w->ps = w->x64 = w->t64 = w->r64 = nullptr;
+    w->b64 = w->r = w->p = w->t = w->ap = w->xs = w->ps = w->x64 = w->t64 = w->r64 = w->x_ds = nullptr;
     w->canon_b = w->canon_r = w->canon_e = w->canon_x = nullptr;
     w->cap = 0;
     w->prec = -1;
@@ -355,6 +356,7 @@ static int ms_workspace(hisq_ctx *ctx, int nshift, int prec) {
         {&w->ap, vector_bytes(prec, Vh, 1)},       {&w->xs, vector_bytes(Q, Vh, 1) * cap},
         {&w->ps, vector_bytes(Q, Vh, 1) * cap},    {&w->x64, vector_bytes(HISQ_FP64, Vh, 1)},
         {&w->t64, vector_bytes(HISQ_FP64, Vh, 1)}, {&w->r64, vector_bytes(HISQ_FP64, Vh, 1)},
+        {&w->x_ds, vector_bytes(HISQ_DS, Vh, 1)},
         {(void **)&w->canon_b, canon},             {(void **)&w->canon_r, canon * cap},
         {(void **)&w->canon_e, canon * cap},       {(void **)&w->canon_x, canon * cap},
     };
@@ -414,7 +416,7 @@ static int ms_enqueue_iteration(hisq_ctx *ctx, MsWork *w, const hisq_links *fat,
     d.out = w->t;
     d.parity = 1;
     d.epi = EPI_PLAIN;
-    const bool use64 = P == HISQ_FP64 && fat->prec != HISQ_FP64;
+    const int use64 = (P == HISQ_FP64 && fat->prec != HISQ_FP64) ? LINKS_FP64 : LINKS_INNER;
     HISQ_CHECK(launch_dslash(ctx, fat, naik, use64, d, nullptr, st));
     d.in = w->t;
     d.out = w->ap;
@@ -521,15 +523,18 @@ static int ms_build(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_
 static int ms_residual(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, const double *x_canon,
                        double mass2, double *res2) {
     cudaStream_t st = ctx->stream;
+    // FP64 accuracy: double-single arithmetic on the ds link copy for low-precision links
+    const int hp = links_hp(fat);
     HISQ_CHECK(pack_vectors(ctx, x_canon, w->x64, 1, HISQ_FP64, st));
+    if (hp == LINKS_DS) HISQ_CHECK(split_vectors(ctx, w->x64, w->x_ds, 1, st));
     DslashArgs d;
     memset(&d, 0, sizeof(d));
     d.n = 1;
-    d.in = w->x64;
+    d.in = hp == LINKS_DS ? w->x_ds : w->x64;
     d.out = w->t64;
     d.parity = 1;
     d.epi = EPI_PLAIN;
-    HISQ_CHECK(launch_dslash(ctx, fat, naik, true, d, nullptr, st));
+    HISQ_CHECK(launch_dslash(ctx, fat, naik, hp, d, nullptr, st));
     d.in = w->t64;
     d.out = w->r64;
     d.parity = 0;
@@ -542,7 +547,7 @@ static int ms_residual(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hi
     d.counter = w->counter;
     d.dot_out = &w->st->res2;
     d.hook = HOOK_NONE;
-    HISQ_CHECK(launch_dslash(ctx, fat, naik, true, d, nullptr, st));
+    HISQ_CHECK(launch_dslash(ctx, fat, naik, hp, d, nullptr, st));
     HISQ_CUDA(cudaMemcpyAsync(res2, &w->st->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
     HISQ_CUDA(cudaStreamSynchronize(st));
     return HISQ_OK;
@@ -577,17 +582,18 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     if (prec != HISQ_FP64 && fat->prec != prec)
         return set_error(HISQ_ERR_ARG, "inner precision %d needs links packed in that precision (links are %d)", prec, fat->prec);
     const double mass2_base = mass * mass + sigma_base;
-    double tol_shared = tol;
+    // the all-FP64 iteration stops at the library's acceptance bound (0.95 tol) like a CG solve
+    double tol_shared = tol * TOL_SAFETY;
     if (prec != HISQ_FP64)
-        tol_shared = std::max(tol, P0.multishift_tol > 0.0 ? P0.multishift_tol : (prec == HISQ_FP32 ? 1e-7 : 1e-4));
+        tol_shared = std::max(tol_shared, P0.multishift_tol > 0.0 ? P0.multishift_tol : (prec == HISQ_FP32 ? 1e-7 : 1e-4));
     HISQ_CHECK(ms_workspace(ctx, nshift, prec));
     MsWork *w = ctx->ms;
     cudaStream_t st = ctx->stream;
     const int Vh = ctx->geom.Vh;
     const size_t vbytes = (size_t)Vh * 6 * sizeof(double);
     if (P0.autotune) {
-        tuned_shape(ctx, fat, naik, 1, prec == HISQ_FP64);
-        tuned_shape(ctx, fat, naik, 1, true);
+        tuned_shape(ctx, fat, naik, 1, prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER);
+        tuned_shape(ctx, fat, naik, 1, links_hp(fat));
     }
 
     // ---- the shared iteration ----

@@ -10,6 +10,7 @@
 
 #include "hisq_internal.cuh"
 #include "dslash_kernel.cuh"
+#include "ds_arith.cuh"
 #include "cg_persistent.cuh"
 
 namespace hisq {
@@ -25,6 +26,7 @@ struct BlasArgs {
     void *r_old;      // Q (flexible CG)
     const void *b;    // FP64 (init)
     void *xhi;        // FP64
+    void *xds;        // x_hi in double-single form, written with x_hi (null: not kept)
     RedArgs red;
     SolverState *st;
     const int *gate;
@@ -217,6 +219,16 @@ __global__ void __launch_bounds__(256) cg_xhi_kernel(BlasArgs a) {
         for (int c = 0; c < 3; c++) xh[c] = {xh[c].re + (double)x[c].re, xh[c].im + (double)x[c].im};
         store_vec<HISQ_FP64>(vxh, s, r, xh);
         store_vec<Q>(vx, s, r, zero);
+        if (a.xds) {
+            float4 *o = reinterpret_cast<float4 *>(a.xds);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float rh, rl, ih, il;
+                ds_split(xh[c].re, rh, rl);
+                ds_split(xh[c].im, ih, il);
+                o[((long)s * 3 + c) * a.n + r] = make_float4(rh, rl, ih, il);
+            }
+        }
     }
 }
 
@@ -343,6 +355,7 @@ struct Workspace {
     int prec = -1;
     void *b_hi = nullptr, *x_hi = nullptr, *x_lo = nullptr, *r_lo = nullptr, *p = nullptr, *Ap = nullptr;
     void *t = nullptr, *t64 = nullptr, *z = nullptr, *r_old = nullptr;
+    void *x_ds = nullptr;         // x_hi in double-single form: input of the residual recomputation
     double *canon = nullptr;      // canonical FP64 staging [cap_n][Vh][6]
     SolverState *st = nullptr;    // device
     SolverState *h_st = nullptr;  // pinned host mirror
@@ -366,10 +379,10 @@ void free_graph(GraphCache &gc) {
 }
 
 static void free_buffers(Workspace *w) {
-    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->canon};
+    void *bufs[] = {w->b_hi, w->x_hi, w->x_lo, w->r_lo, w->p, w->Ap, w->t, w->t64, w->z, w->r_old, w->x_ds, w->canon};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = nullptr;
+    w->b_hi = w->x_hi = w->x_lo = w->r_lo = w->p = w->Ap = w->t = w->t64 = w->z = w->r_old = w->x_ds = nullptr;
     w->canon = nullptr;
     w->cap_n = 0;
     w->prec = -1;
@@ -409,6 +422,7 @@ static int ensure_workspace(hisq_ctx *ctx, int n, int prec, bool need_pc) {
         {&w->x_lo, vector_bytes(Q, Vh, cap)},         {&w->r_lo, vector_bytes(Q, Vh, cap)},
         {&w->p, vector_bytes(prec, Vh, cap)},         {&w->Ap, vector_bytes(prec, Vh, cap)},
         {&w->t, vector_bytes(prec, Vh, cap)},         {&w->t64, vector_bytes(HISQ_FP64, Vh, cap)},
+        {&w->x_ds, vector_bytes(HISQ_DS, Vh, cap)},
         {(void **)&w->canon, (size_t)cap * Vh * 6 * sizeof(double)},
     };
     for (auto &a : allocs)
@@ -466,6 +480,8 @@ struct Solve {
     hisq_solve_stats *stats = nullptr;
     const double *mass2v = nullptr;  // per right-hand side m^2 (shifted systems; persistent driver only)
     const double *tolv = nullptr;    // per right-hand side relative tolerance (or null: the solve's tol)
+    int hp = LINKS_FP64;             // links and arithmetic of the residual recomputation (LINKS_DS
+                                     // for mixed precision, LINKS_FP64 for plain FP64 solves)
 };
 
 static BlasArgs blas_args(const Solve &S) {
@@ -485,6 +501,7 @@ static BlasArgs blas_args(const Solve &S) {
     a.r_old = S.w->r_old;
     a.b = S.w->b_hi;
     a.xhi = S.w->x_hi;
+    a.xds = S.hp == LINKS_DS ? S.w->x_ds : nullptr;
     a.red.partials = S.w->partials;
     a.red.counter = S.w->counter;
     a.red.dot_out = S.w->dots;
@@ -538,7 +555,7 @@ static int blas(const Solve &S, int which) {
     }
 }
 
-static int dslash_step(const Solve &S, DslashArgs d, bool use64, int *grid_out = nullptr) {
+static int dslash_step(const Solve &S, DslashArgs d, int copy, int *grid_out = nullptr) {
     if (!d.partials_only) d.partials = S.w->partials;
     d.partials_cap = S.w->partials_cap;
     d.counter = S.w->counter;
@@ -550,27 +567,29 @@ static int dslash_step(const Solve &S, DslashArgs d, bool use64, int *grid_out =
         cudaEventCreate(&e1);
         cudaEventRecord(e0, S.st);
     }
-    int rc = launch_dslash(S.ctx, S.fat, S.naik, use64, d, nullptr, S.st, grid_out);
+    int rc = launch_dslash(S.ctx, S.fat, S.naik, copy, d, nullptr, S.st, grid_out);
     if (S.timing) {
         cudaEventRecord(e1, S.st);
-        (use64 ? S.events64 : S.events)->push_back({e0, e1});
+        (copy != LINKS_INNER ? S.events64 : S.events)->push_back({e0, e1});
     }
     return rc;
 }
 
-// the reliable update: x_hi += x_lo; t64 = D_oe x_hi; r_lo = b - A x_hi (FP64) -> HOOK_RELIABLE
+// the reliable update: x_hi += x_lo; t64 = D_oe x_hi; r_lo = b - A x_hi (FP64 accuracy: double-
+// single Dslash on the ds copy of x_hi, FP64 epilogue; native FP64 for plain FP64 solves)
+// -> HOOK_RELIABLE
 static int enqueue_update(const Solve &S) {
     HISQ_CHECK(blas(S, -1));
     DslashArgs d;
     memset(&d, 0, sizeof(d));
     d.n = S.n;
-    d.in = S.w->x_hi;
+    d.in = S.hp == LINKS_DS ? S.w->x_ds : S.w->x_hi;
     d.out = S.w->t64;
     d.parity = 1;
     d.epi = EPI_PLAIN;
     d.active = S.w->st->update;
     d.gate = &S.w->st->any_update;
-    HISQ_CHECK(dslash_step(S, d, true));
+    HISQ_CHECK(dslash_step(S, d, S.hp));
     d.in = S.w->t64;
     d.out = nullptr;
     d.parity = 0;
@@ -581,7 +600,7 @@ static int enqueue_update(const Solve &S) {
     d.out_lo = S.w->r_lo;
     d.lo_prec = q_prec(S.prec);
     d.hook = HOOK_RELIABLE;
-    return dslash_step(S, d, true);
+    return dslash_step(S, d, S.hp);
 }
 
 // one CG iteration up to the decision: t = D_oe p; Ap = m^2 p - D_eo t (pAp -> alpha);
@@ -595,7 +614,7 @@ static int enqueue_iteration_head(const Solve &S) {
     d.parity = 1;
     d.epi = EPI_PLAIN;
     d.active = S.w->st->active;
-    const bool sloppy64 = S.prec == HISQ_FP64;  // plain FP64 CG reads the FP64 link copy
+    const int sloppy64 = S.prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER;  // plain FP64 CG reads the FP64 link copy
     HISQ_CHECK(dslash_step(S, d, sloppy64));
     d.in = S.w->t;
     d.out = S.w->Ap;
@@ -840,7 +859,7 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     *done = false;
     if (S.pc || S.naik->recon != 18) return HISQ_OK;
     Workspace *w = S.w;
-    LaunchShape sh = tuned_shape(S.ctx, S.fat, S.naik, S.n, S.prec == HISQ_FP64);
+    LaunchShape sh = tuned_shape(S.ctx, S.fat, S.naik, S.n, S.prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER);
     int R = sh.R > 4 ? 4 : sh.R;
     if (S.prec == HISQ_FP64 && R > 2) R = 2;  // four FP64 right-hand sides per thread would spill
     while (S.n % R) R /= 2;
@@ -862,11 +881,16 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     a.g = S.ctx->geom;
     a.fat = S.fat->field();
     a.naik = S.naik->field();
-    a.fat64 = S.fat->field64();
-    a.naik64 = S.naik->field64();
     if (S.prec == HISQ_FP64) {
+        a.fat64 = S.fat->field64();
+        a.naik64 = S.naik->field64();
         a.fat = a.fat64;
         a.naik = a.naik64;
+    } else {
+        // the residual recomputation in double-single arithmetic on the ds link copies
+        a.fat64 = S.fat->field_ds();
+        a.naik64 = S.naik->field_ds();
+        a.xds = w->x_ds;
     }
     a.p = w->p;
     a.t = w->t;
@@ -999,7 +1023,7 @@ int cg_solve_common(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik
             return set_error(HISQ_ERR_ARG, "flexible CG with the network needs FP32 inner precision and FP32 links");
         if (P.pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
     }
-    int bundle = P.bundle > 0 ? P.bundle : choose_bundle(ctx, fat, naik, nrhs, prec == HISQ_FP64);
+    int bundle = P.bundle > 0 ? P.bundle : choose_bundle(ctx, fat, naik, nrhs, prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER);
     bundle = std::min(bundle, nrhs);
     HISQ_CHECK(ensure_workspace(ctx, bundle, prec, P.pc != nullptr));
     if (P.pc) HISQ_CHECK(pc_prepare(ctx, P.pc, bundle));
@@ -1026,9 +1050,10 @@ int cg_solve_common(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik
         S.tolv = tolv ? tolv + k0 : nullptr;
         if (mass2v) S.timing = false;  // shifted bundles run on the persistent driver only
         // tune (outside any capture) before the first use of this shape
+        S.hp = prec == HISQ_FP64 ? LINKS_FP64 : links_hp(fat);
         if (P.autotune) {
-            tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64);
-            tuned_shape(ctx, fat, naik, n, true);
+            tuned_shape(ctx, fat, naik, n, prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER);
+            tuned_shape(ctx, fat, naik, n, S.hp);
         }
         for (int k = 0; k < n; k++)
             HISQ_CUDA(cudaMemcpyAsync(w->canon + (size_t)k * Vh * 6, rhs[k0 + k], vbytes, cudaMemcpyDefault, ctx->stream));
@@ -1064,6 +1089,7 @@ int cg_solve_common(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik
         else
             stats.kernel_launches += 3 + per_iter * h.bundle_iters + 3L * (graph_mode ? h.update_rounds : h.bundle_iters);
         stats.bundle_iterations += bmax;
+        stats.recompute_passes += h.update_rounds;
         stats.bundles++;
     }
     for (int which = 0; which < 2; which++) {

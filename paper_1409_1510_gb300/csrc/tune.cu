@@ -10,7 +10,7 @@ namespace hisq {
 
 // Median launch time of one shape; each timed launch follows an L2 flush (a write larger than
 // L2) so the links come from HBM, as they do inside a solve, and the parity alternates.
-static int time_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, bool use64, int n,
+static int time_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int copy, int n,
                       const LaunchShape &sh, void *in, void *out, void *flush, size_t flush_bytes, float *ms_out) {
     DslashArgs d;
     memset(&d, 0, sizeof(d));
@@ -24,12 +24,12 @@ static int time_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *na
         cudaEventCreate(&e0[i]);
         cudaEventCreate(&e1[i]);
     }
-    int rc = launch_dslash(ctx, fat, naik, use64, d, &sh, ctx->stream);  // warm-up
+    int rc = launch_dslash(ctx, fat, naik, copy, d, &sh, ctx->stream);  // warm-up
     for (int i = 0; i < 5 && rc == HISQ_OK; i++) {
         if (flush) cudaMemsetAsync(flush, i, flush_bytes, ctx->stream);
         d.parity = i & 1;
         cudaEventRecord(e0[i], ctx->stream);
-        rc = launch_dslash(ctx, fat, naik, use64, d, &sh, ctx->stream);
+        rc = launch_dslash(ctx, fat, naik, copy, d, &sh, ctx->stream);
         cudaEventRecord(e1[i], ctx->stream);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -47,9 +47,9 @@ static int time_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *na
     return rc;
 }
 
-static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64, LaunchShape *best,
+static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, int copy, LaunchShape *best,
                      float *best_ms_out) {
-    int prec = use64 ? HISQ_FP64 : fat->prec;
+    int prec = copy_prec(fat, copy);
     size_t bytes = vector_bytes(prec, ctx->geom.Vh, n);
     void *in = nullptr, *out = nullptr;
     if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
@@ -68,12 +68,14 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     const int Rs[] = {1, 2, 4, 8};
     const int Ts[] = {256, 128, 64, 32};
     int rc = HISQ_OK;
-    const int recon = use64 ? 18 : naik->recon;
+    const int recon = copy != LINKS_INNER ? 18 : naik->recon;
     const int words = link_words(prec, 18) + link_words(prec, recon);
     for (int R : Rs) {
         if (n % R != 0) continue;
         if (prec == HISQ_FP64 && R > 4) continue;
+        if (prec == HISQ_DS && R > 2) continue;  // double-single: one or two RHS per thread, no lane split
         for (int S = 1; S <= 8; S *= 2) {
+        if (S > 1 && prec == HISQ_DS) continue;
         if (S > 1 && (recon != 18 || R > 8 / std::min(S, 4))) continue;
         if (S == 8 && (prec == HISQ_FP64 || R > 2)) continue;
         for (int T : Ts) {
@@ -87,7 +89,7 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
                     continue;
             }
             float ms = 0;
-            rc = time_shape(ctx, fat, naik, use64, n, sh, in, out, flush, flush_bytes, &ms);
+            rc = time_shape(ctx, fat, naik, copy, n, sh, in, out, flush, flush_bytes, &ms);
             if (rc != HISQ_OK) break;
             // a candidate replaces the incumbent only if it is clearly faster (2%): the
             // candidates are ordered from the simplest shape, and noise must not pick a shape
@@ -108,9 +110,9 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     return rc;
 }
 
-LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, bool use64) {
-    int prec = use64 ? HISQ_FP64 : fat->prec;
-    int recon = use64 ? 18 : naik->recon;
+LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int n, int copy) {
+    int prec = copy_prec(fat, copy);
+    int recon = copy != LINKS_INNER ? 18 : naik->recon;
     TuneKey key{prec, recon, n, 0};
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
@@ -120,7 +122,7 @@ LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *
     if (cs != cudaStreamCaptureStatusNone) return default_shape(prec, n);
     LaunchShape best;
     float ms = 0.0f;
-    if (run_tuner(ctx, fat, naik, n, use64, &best, &ms) != HISQ_OK) {
+    if (run_tuner(ctx, fat, naik, n, copy, &best, &ms) != HISQ_OK) {
         best = default_shape(prec, n);
         ms = 0.0f;
     }
@@ -136,13 +138,13 @@ LaunchShape tuned_shape(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *
 // one for the remainder).  Every solver kernel streams the links once per bundle step and the
 // vectors once per right-hand side, as the Dslash does, so its time is the model.  Falls back to
 // the largest bundle when a time is unknown (tuning off or failed).
-int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, bool use64) {
+int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int nrhs, int copy) {
     const int cap = std::min(nrhs, HISQ_MAX_BUNDLE);
     if (!ctx->params.autotune) return cap;
-    const int prec = use64 ? HISQ_FP64 : fat->prec;
-    const int recon = use64 ? 18 : naik->recon;
+    const int prec = copy_prec(fat, copy);
+    const int recon = copy != LINKS_INNER ? 18 : naik->recon;
     auto time_of = [&](int n, float *ms) {
-        tuned_shape(ctx, fat, naik, n, use64);
+        tuned_shape(ctx, fat, naik, n, copy);
         auto it = ctx->tuned_ms.find(TuneKey{prec, recon, n, 0});
         if (it == ctx->tuned_ms.end()) return false;
         *ms = it->second;
@@ -184,7 +186,7 @@ extern "C" int hisq_autotune(const hisq_links *fat, const hisq_links *naik, int 
     ctx->tuned.erase(key);
     LaunchShape best;
     float ms = 0.0f;
-    HISQ_CHECK(run_tuner(ctx, fat, naik, nrhs, false, &best, &ms));
+    HISQ_CHECK(run_tuner(ctx, fat, naik, nrhs, LINKS_INNER, &best, &ms));
     ctx->tuned[key] = best;
     if (ms > 0.0f && ms < 1e29f) ctx->tuned_ms[key] = ms;
     ctx->tune_generation++;

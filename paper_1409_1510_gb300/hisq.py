@@ -49,7 +49,7 @@ class hisq_solve_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_long), ("solve_kernel_ms", ctypes.c_double),
                 ("solve_kernel_launches", ctypes.c_int), ("phase_ms", ctypes.c_double * 5),
                 ("shared_iterations", ctypes.c_int), ("refine_iterations", ctypes.c_long),
-                ("shared_seconds", ctypes.c_double)]
+                ("shared_seconds", ctypes.c_double), ("recompute_passes", ctypes.c_long)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -74,6 +74,7 @@ _SIGNATURES = {
     "hisq_dslash": ([_VP, _VP, _VP, _VP, _I, _I], _I),
     "hisq_aop": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
     "hisq_aop_noalloc": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
+    "hisq_residual": ([_VP, _VP, _D, _VP, _VP, _VP, _I, _VP], _I),
     "hisq_default_solver_params": ([ctypes.POINTER(hisq_solver_params)], None),
     "hisq_set_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
@@ -192,6 +193,11 @@ def hisq_dslash(fat, naik, vin, vout, nrhs: int, parity: int):
 
 def hisq_aop(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
     _check(load().hisq_aop(fat, naik, float(mass), _ptr(vin), _ptr(vout), int(nrhs), _ptr(pAp)))
+
+
+def hisq_residual(fat, naik, mass: float, rhs, x, r, nrhs: int, res2=None):
+    """r = rhs - A x in FP64 accuracy (canonical buffers, host or device); see include/hisq.h."""
+    _check(load().hisq_residual(fat, naik, float(mass), _ptr(rhs), _ptr(x), _ptr(r), int(nrhs), _ptr(res2)))
 
 
 def hisq_aop_noalloc(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
