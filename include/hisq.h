@@ -158,6 +158,33 @@ int hisq_aop(const hisq_links *fat, const hisq_links *naik, double mass, const v
 int hisq_residual(const hisq_links *fat, const hisq_links *naik, double mass, const double *rhs,
                   const double *x, double *r, int nrhs, double *res2);
 
+/* ---- domain decomposition along t (the lattice split over accelerators) ------------------- */
+
+#define HISQ_MAX_SLABS 8
+
+typedef struct hisq_slabs hisq_slabs;
+
+/* Cut the context's lattice along t into nslab slabs of Lt / nslab time planes (an even number,
+ * at least 4) held on this GPU as a multi-GPU run would hold them on several: each slab keeps the
+ * gathered link records of its own output sites in precision prec (18 reals per link; the
+ * backward links at its lower end come from the neighbouring slab at pack time) and its own
+ * vectors with three ghost time planes at either end, the reach of the Naik term (Eq. (3):
+ * hops of 1 and 3).  fat, naik: device canonical double[4][V][3][3][2] (as hisq_links_create).
+ * Allocates the slabs' storage. */
+int hisq_slabs_create(hisq_slabs **h, const double *fat, const double *naik, int prec, int nslab);
+int hisq_slabs_destroy(hisq_slabs *h);
+
+/* out = D_{parity, 1-parity} in (Eq. (3)-(4), nrhs right-hand sides) through the decomposition:
+ * the input is scattered into the slabs; each slab packs its three outgoing planes at either end
+ * (face-pack kernel); the faces are copied into the neighbours' ghost planes on a second stream
+ * (cudaMemcpyAsync) while the interior kernel computes the output planes whose +-3 neighbours are
+ * the slab's own; the boundary kernels then compute the three planes at either end; the outputs
+ * are gathered.  in, out: device canonical double[nrhs][V/2][3][2] (in on parity 1 - parity).
+ * ms (host, may be NULL) receives four CUDA-event times in milliseconds: face packing, the
+ * interior kernels, the halo copies, and the decomposed Dslash from face packing to the last
+ * boundary kernel. */
+int hisq_slabs_dslash(hisq_slabs *h, const double *in, double *out, int nrhs, int parity, double *ms);
+
 /* ---- A-operator without allocation -------------------------------------------------------- */
 
 /* Size of the static device scratch behind hisq_aop_noalloc (per device, held until exit). */

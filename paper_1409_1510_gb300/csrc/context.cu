@@ -79,11 +79,10 @@ __device__ inline int lex_shift(const Geom &g, const int c[4], int mu, int step)
     return d[0] + g.L[0] * (d[1] + g.L[1] * (d[2] + g.L[2] * d[3]));
 }
 
-// gathered link `slot` of output site (s, parity): slot 2mu = U_{x,mu}; 2mu+1 = -U^dag_{x-hop mu,mu}
-__device__ inline void gathered_link(const Geom &g, const double *U, int s, int parity, int slot, int hop,
+// gathered link `slot` of the output site at lattice coordinates c (lexicographic index x):
+// slot 2mu = U_{x,mu}; 2mu+1 = -U^dag_{x-hop mu,mu}
+__device__ inline void gathered_link(const Geom &g, const double *U, const int c[4], int x, int slot, int hop,
                                      C64 M[3][3]) {
-    int c[4];
-    int x = lex_of_eo(g, s, parity, c);
     int mu = slot >> 1;
     long V = 2L * g.Vh;
     if ((slot & 1) == 0) {
@@ -121,13 +120,22 @@ __device__ inline void put_real(uint4 *words, int Vh, int W, int parity, int s, 
     else *reinterpret_cast<__nv_bfloat16 *>(base) = __double2bfloat16(val);
 }
 
+// Records of the output sites of the storage lattice gs (the lattice itself, or one slab of it
+// with ghost planes): storage site (x, y, z, ts) is the lattice site (x, y, z, (ts + t_off) mod Lt)
+// and only planes ts in [t_lo, t_hi) are packed; t_off is even, so both agree on parity.
 template <int P, int RECON>
-__global__ void pack_links_kernel(Geom g, const double *U, int hop, uint4 *words, float *scale, int W) {
+__global__ void pack_links_kernel(Geom g, Geom gs, int t_off, int t_lo, int t_hi, const double *U, int hop,
+                                  uint4 *words, float *scale, int W) {
     long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= 2L * g.Vh) return;
-    int parity = (int)(i / g.Vh), s = (int)(i % g.Vh);
+    if (i >= 2L * gs.Vh) return;
+    int parity = (int)(i / gs.Vh), s = (int)(i % gs.Vh);
+    int c[4];
+    lex_of_eo(gs, s, parity, c);
+    if (c[3] < t_lo || c[3] >= t_hi) return;
+    c[3] = (c[3] + t_off) % g.L[3];
+    const int x = c[0] + g.L[0] * (c[1] + g.L[1] * (c[2] + g.L[2] * c[3]));
     C64 M[8][3][3];
-    for (int k = 0; k < 8; k++) gathered_link(g, U, s, parity, k, hop, M[k]);
+    for (int k = 0; k < 8; k++) gathered_link(g, U, c, x, k, hop, M[k]);
     double sc = 1.0;
     if (RECON == 18 && scale) {
         double m = 0.0;
@@ -135,15 +143,15 @@ __global__ void pack_links_kernel(Geom g, const double *U, int hop, uint4 *words
             for (int a = 0; a < 3; a++)
                 for (int b = 0; b < 3; b++) m = fmax(m, fmax(fabs(M[k][a][b].re), fabs(M[k][a][b].im)));
         sc = m > 0.0 ? m : 1.0;
-        scale[(size_t)parity * g.Vh + s] = (float)sc;
+        scale[(size_t)parity * gs.Vh + s] = (float)sc;
     }
     for (int k = 0; k < 8; k++) {
         int o = k * RECON;
         if (RECON == 18) {
             for (int a = 0; a < 3; a++)
                 for (int b = 0; b < 3; b++) {
-                    put_real<P>(words, g.Vh, W, parity, s, o + 6 * a + 2 * b, M[k][a][b].re / sc);
-                    put_real<P>(words, g.Vh, W, parity, s, o + 6 * a + 2 * b + 1, M[k][a][b].im / sc);
+                    put_real<P>(words, gs.Vh, W, parity, s, o + 6 * a + 2 * b, M[k][a][b].re / sc);
+                    put_real<P>(words, gs.Vh, W, parity, s, o + 6 * a + 2 * b + 1, M[k][a][b].im / sc);
                 }
             continue;
         }
@@ -164,22 +172,22 @@ __global__ void pack_links_kernel(Geom g, const double *U, int hop, uint4 *words
             for (int b = 0; b < 3; b++) Wm[a][b] = {A[a][b].re * ic, A[a][b].im * ic};
         if (RECON == 13) {
             for (int b = 0; b < 3; b++) {
-                put_real<P>(words, g.Vh, W, parity, s, o + 2 * b, Wm[0][b].re);
-                put_real<P>(words, g.Vh, W, parity, s, o + 2 * b + 1, Wm[0][b].im);
-                put_real<P>(words, g.Vh, W, parity, s, o + 6 + 2 * b, Wm[1][b].re);
-                put_real<P>(words, g.Vh, W, parity, s, o + 7 + 2 * b, Wm[1][b].im);
+                put_real<P>(words, gs.Vh, W, parity, s, o + 2 * b, Wm[0][b].re);
+                put_real<P>(words, gs.Vh, W, parity, s, o + 2 * b + 1, Wm[0][b].im);
+                put_real<P>(words, gs.Vh, W, parity, s, o + 6 + 2 * b, Wm[1][b].re);
+                put_real<P>(words, gs.Vh, W, parity, s, o + 7 + 2 * b, Wm[1][b].im);
             }
-            put_real<P>(words, g.Vh, W, parity, s, o + 12, 24.0 * c);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 12, 24.0 * c);
         } else {
-            put_real<P>(words, g.Vh, W, parity, s, o + 0, atan2(Wm[0][0].im, Wm[0][0].re));
-            put_real<P>(words, g.Vh, W, parity, s, o + 1, atan2(Wm[2][0].im, Wm[2][0].re));
-            put_real<P>(words, g.Vh, W, parity, s, o + 2, Wm[0][1].re);
-            put_real<P>(words, g.Vh, W, parity, s, o + 3, Wm[0][1].im);
-            put_real<P>(words, g.Vh, W, parity, s, o + 4, Wm[0][2].re);
-            put_real<P>(words, g.Vh, W, parity, s, o + 5, Wm[0][2].im);
-            put_real<P>(words, g.Vh, W, parity, s, o + 6, Wm[1][0].re);
-            put_real<P>(words, g.Vh, W, parity, s, o + 7, Wm[1][0].im);
-            put_real<P>(words, g.Vh, W, parity, s, o + 8, 24.0 * c);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 0, atan2(Wm[0][0].im, Wm[0][0].re));
+            put_real<P>(words, gs.Vh, W, parity, s, o + 1, atan2(Wm[2][0].im, Wm[2][0].re));
+            put_real<P>(words, gs.Vh, W, parity, s, o + 2, Wm[0][1].re);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 3, Wm[0][1].im);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 4, Wm[0][2].re);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 5, Wm[0][2].im);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 6, Wm[1][0].re);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 7, Wm[1][0].im);
+            put_real<P>(words, gs.Vh, W, parity, s, o + 8, 24.0 * c);
         }
     }
 }
@@ -212,13 +220,16 @@ __global__ void export_links_kernel(Geom g, LinkField f, double *out) {
 }
 
 template <int P>
-static void launch_pack(int recon, const Geom &g, const double *U, int hop, uint4 *words, float *scale, int W,
-                        cudaStream_t st) {
+static void launch_pack(int recon, const Geom &g, const Geom &gs, int t_off, int t_lo, int t_hi, const double *U,
+                        int hop, uint4 *words, float *scale, int W, cudaStream_t st) {
     int threads = 128;
-    int blocks = (int)((2L * g.Vh + threads - 1) / threads);
-    if (recon == 13) pack_links_kernel<P, 13><<<blocks, threads, 0, st>>>(g, U, hop, words, scale, W);
-    else if (recon == 9) pack_links_kernel<P, 9><<<blocks, threads, 0, st>>>(g, U, hop, words, scale, W);
-    else pack_links_kernel<P, 18><<<blocks, threads, 0, st>>>(g, U, hop, words, scale, W);
+    int blocks = (int)((2L * gs.Vh + threads - 1) / threads);
+    if (recon == 13)
+        pack_links_kernel<P, 13><<<blocks, threads, 0, st>>>(g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W);
+    else if (recon == 9)
+        pack_links_kernel<P, 9><<<blocks, threads, 0, st>>>(g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W);
+    else
+        pack_links_kernel<P, 18><<<blocks, threads, 0, st>>>(g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W);
 }
 
 template <int P>
@@ -230,15 +241,20 @@ static void launch_export(int recon, const Geom &g, LinkField f, double *out, cu
     else export_links_kernel<P, 18><<<blocks, threads, 0, st>>>(g, f, out);
 }
 
+void pack_links_into(int prec, int recon, const Geom &g, const Geom &gs, int t_off, int t_lo, int t_hi,
+                     const double *U, int hop, uint4 *words, float *scale, int W, cudaStream_t st) {
+    switch (prec) {
+    case HISQ_DS: launch_pack<HISQ_DS>(18, g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W, st); break;
+    case HISQ_FP64: launch_pack<HISQ_FP64>(recon, g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W, st); break;
+    case HISQ_FP32: launch_pack<HISQ_FP32>(recon, g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W, st); break;
+    case HISQ_FP16: launch_pack<HISQ_FP16>(recon, g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W, st); break;
+    default: launch_pack<HISQ_BF16>(recon, g, gs, t_off, t_lo, t_hi, U, hop, words, scale, W, st); break;
+    }
+}
+
 static void dispatch_pack(int prec, int recon, const Geom &g, const double *U, int hop, uint4 *words, float *scale,
                           int W, cudaStream_t st) {
-    switch (prec) {
-    case HISQ_DS: launch_pack<HISQ_DS>(18, g, U, hop, words, scale, W, st); break;
-    case HISQ_FP64: launch_pack<HISQ_FP64>(recon, g, U, hop, words, scale, W, st); break;
-    case HISQ_FP32: launch_pack<HISQ_FP32>(recon, g, U, hop, words, scale, W, st); break;
-    case HISQ_FP16: launch_pack<HISQ_FP16>(recon, g, U, hop, words, scale, W, st); break;
-    default: launch_pack<HISQ_BF16>(recon, g, U, hop, words, scale, W, st); break;
-    }
+    pack_links_into(prec, recon, g, g, 0, 0, g.L[3], U, hop, words, scale, W, st);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -329,6 +345,9 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int prec = copy_prec(fat, copy);
     int recon = copy != LINKS_INNER ? 18 : naik->recon;
     if (ds && d.epi == EPI_AOP) return set_error(HISQ_ERR_ARG, "double-single Dslash has no A-operator epilogue");
+    if ((d.geom || d.fields) && (!d.geom || !d.fields || !shape))
+        return set_error(HISQ_ERR_ARG, "a Dslash on another lattice needs its geometry, links and launch shape");
+    const Geom &G = d.geom ? *d.geom : ctx->geom;
     LaunchShape sh = shape ? *shape : tuned_shape(ctx, fat, naik, d.n, copy);
     int R = sh.R;
     if (R != 1 && R != 2 && R != 4 && R != 8) R = 1;
@@ -339,7 +358,9 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int S = 1;
     if (!ds && recon == 18 && sh.S == 2 && R <= 4) S = 2;
     if (!ds && recon == 18 && sh.S == 4 && R <= 2) S = 4;
-    if (!ds && recon == 18 && sh.S == 8 && R <= 2 && prec != HISQ_FP64 && d.epi != EPI_RESID) S = 8;
+    const bool ranged = d.site_end > 0;  // the staged kernel covers whole parities only
+    if (!ds && !ranged && recon == 18 && sh.S == 8 && R <= 2 && prec != HISQ_FP64 && d.epi != EPI_RESID) S = 8;
+    if (!ds && ranged && recon == 18 && sh.S == 8 && R <= 2) S = 4;
     int t = (d.n + R - 1) / R;
     // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
     // threads keep both the partial count and that block's share of the sum small
@@ -358,9 +379,13 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
 
     KArgs a;
     memset(&a, 0, sizeof(a));
-    a.g = ctx->geom;
+    a.g = G;
     a.fat = ds ? fat->field_ds() : copy == LINKS_FP64 ? fat->field64() : fat->field();
     a.naik = ds ? naik->field_ds() : copy == LINKS_FP64 ? naik->field64() : naik->field();
+    if (d.fields) {
+        a.fat = d.fields[0];
+        a.naik = d.fields[1];
+    }
     a.in = d.in;
     a.out = d.out;
     a.n = d.n;
@@ -381,6 +406,14 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     a.red.st = reinterpret_cast<SolverState *>(d.hook_state);
     a.red.partials_only = d.partials_only;
     a.err = ctx->dev_err;
+    a.s0 = 0;
+    a.s1 = G.Vh;
+    if (ranged) {
+        if (d.site_begin < 0 || d.site_end > G.Vh || d.site_begin >= d.site_end)
+            return set_error(HISQ_ERR_ARG, "output site range [%d, %d) outside the parity", d.site_begin, d.site_end);
+        a.s0 = d.site_begin;
+        a.s1 = d.site_end;
+    }
 
     size_t smem = 0;
     if (S == 8) {
@@ -392,7 +425,7 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     } else if (d.epi != EPI_PLAIN) {
         size_t need = std::max((size_t)spb * d.n, (size_t)threads + 64);
         smem = need * sizeof(double);
-        long tiles = (ctx->geom.Vh + spb - 1) / spb;
+        long tiles = (a.s1 - a.s0 + spb - 1) / spb;
         // the grid never exceeds one resident wave per SM times 64, nor the tile count
         size_t max_grid = (size_t)std::min<long>(tiles, (long)ctx->num_sms * 64);
         if (!d.partials || !d.counter || max_grid * d.n > d.partials_cap)

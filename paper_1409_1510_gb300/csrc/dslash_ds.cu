@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(256) dslash_ds_kernel(KArgs a) {
 #pragma unroll
     for (int r = 0; r < R; r++) dot[r] = 0.0;
 
-    for (int tile = blockIdx.x; (long)tile * a.spb < g.Vh; tile += gridDim.x) {
-        const int s = tile * a.spb + sl;
-        if (!(sl < a.spb && s < g.Vh && any_act)) continue;
+    for (int tile = blockIdx.x; (long)tile * a.spb < a.s1 - a.s0; tile += gridDim.x) {
+        const int s = a.s0 + tile * a.spb + sl;
+        if (!(sl < a.spb && s < a.s1 && any_act)) continue;
         dscplx acc[R][3];
         ds_site_stencil<R, false>(g, a.fat, a.naik, a.parity, in, a.n, s, r0, act, acc);
         if constexpr (EPI == EPI_PLAIN) {
@@ -106,7 +106,7 @@ template <int R, int EPI>
 static cudaError_t launch_ds_one(const KArgs &a, int threads, size_t smem, int num_sms, cudaStream_t stream,
                                  int *grid_out) {
     auto k = dslash_ds_kernel<R, EPI>;
-    long tiles = (a.g.Vh + a.spb - 1) / a.spb;
+    long tiles = (a.s1 - a.s0 + a.spb - 1) / a.spb;
     int grid = (int)balanced_grid(tiles, wave_grid(k, threads, smem, num_sms, tiles));
     if (grid_out) *grid_out = grid;
     k<<<grid, threads, smem, stream>>>(a);

@@ -43,6 +43,8 @@ struct KArgs {
     const int *gate;
     RedArgs red;
     int *err;        // staged kernel: set when a bounded wait for a staged tile runs out
+    int s0, s1;      // output sites [s0, s1) of the parity (the whole parity: 0, Vh); the staged
+                     // kernel always covers the whole parity
 };
 
 template <int P>
@@ -323,9 +325,9 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 #pragma unroll
     for (int r = 0; r < R; r++) dot[r] = 0.0;
 
-    for (int tile = blockIdx.x; (long)tile * a.spb < g.Vh; tile += gridDim.x) {
-        const int s = tile * a.spb + sl;
-        const bool valid = sl < a.spb && s < g.Vh && any_act;
+    for (int tile = blockIdx.x; (long)tile * a.spb < a.s1 - a.s0; tile += gridDim.x) {
+        const int s = a.s0 + tile * a.spb + sl;
+        const bool valid = sl < a.spb && s < a.s1 && any_act;
         if (S == 1 && !valid) continue;
 
         Cplx<real> acc[R][3];

@@ -24,7 +24,7 @@ inline cudaError_t launch_one(const KArgs &a, int threads, size_t smem, int num_
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    long tiles = (a.g.Vh + a.spb - 1) / a.spb;
+    long tiles = (a.s1 - a.s0 + a.spb - 1) / a.spb;
     int grid = wave_grid(k, threads, smem, num_sms, tiles);
     // one full wave, every block with the same number of tiles
     grid = (int)balanced_grid(tiles, grid);

@@ -388,6 +388,12 @@ struct DslashArgs {
     int hook;              // solver hook run by the last block (0 = none)
     void *hook_state;
     int partials_only;     // reducing epilogues: publish per-block partials only (no finish)
+    int site_begin, site_end;  // output sites [site_begin, site_end) of the parity; 0, 0 = all
+    // another lattice and link records than the context's (a slab of the domain decomposition):
+    // used instead of ctx->geom and the handles' copies when set; the handles then only give the
+    // precision and encoding, and the caller passes the launch shape
+    const Geom *geom;
+    const LinkField *fields;   // [2]: fat, Naik
 };
 // Which copy of the links a Dslash reads, and in which arithmetic: the handle's own storage
 // precision; the FP64 copy in FP64; or the double-single copy in double-single arithmetic (input
@@ -405,6 +411,11 @@ int choose_bundle(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
 inline int copy_prec(const hisq_links *fat, int copy) {
     return copy == LINKS_DS ? HISQ_DS : copy == LINKS_FP64 ? HISQ_FP64 : fat->prec;
 }
+// Gathered link records (context.cu) of the storage lattice gs for links U of the lattice g: storage
+// site (x, y, z, ts) is lattice site (x, y, z, (ts + t_off) mod Lt), only planes ts in [t_lo, t_hi)
+// (gs = g, t_off = 0: the whole lattice; otherwise one slab with ghost planes)
+void pack_links_into(int prec, int recon, const Geom &g, const Geom &gs, int t_off, int t_lo, int t_hi,
+                     const double *U, int hop, uint4 *words, float *scale, int W, cudaStream_t st);
 // FP64 bundle -> double-single bundle of n right-hand sides (dslash_ds.cu)
 int split_vectors(hisq_ctx *ctx, const void *fp64_bundle, void *ds_bundle, int n, cudaStream_t st);
 void free_workspace(hisq_ctx *ctx);  // solver.cu

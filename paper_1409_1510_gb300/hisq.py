@@ -75,6 +75,9 @@ _SIGNATURES = {
     "hisq_aop": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
     "hisq_aop_noalloc": ([_VP, _VP, _D, _VP, _VP, _I, _VP], _I),
     "hisq_residual": ([_VP, _VP, _D, _VP, _VP, _VP, _I, _VP], _I),
+    "hisq_slabs_create": ([ctypes.POINTER(_VP), _VP, _VP, _I, _I], _I),
+    "hisq_slabs_destroy": ([_VP], _I),
+    "hisq_slabs_dslash": ([_VP, _VP, _VP, _I, _I, _VP], _I),
     "hisq_default_solver_params": ([ctypes.POINTER(hisq_solver_params)], None),
     "hisq_set_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
     "hisq_get_solver_params": ([ctypes.POINTER(hisq_solver_params)], _I),
@@ -198,6 +201,21 @@ def hisq_aop(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
 def hisq_residual(fat, naik, mass: float, rhs, x, r, nrhs: int, res2=None):
     """r = rhs - A x in FP64 accuracy (canonical buffers, host or device); see include/hisq.h."""
     _check(load().hisq_residual(fat, naik, float(mass), _ptr(rhs), _ptr(x), _ptr(r), int(nrhs), _ptr(res2)))
+
+
+def hisq_slabs_create(fat_canon, naik_canon, prec: int, nslab: int = 2):
+    h = _VP()
+    _check(load().hisq_slabs_create(ctypes.byref(h), _ptr(fat_canon), _ptr(naik_canon), int(prec), int(nslab)))
+    return h
+
+
+def hisq_slabs_destroy(h):
+    _check(load().hisq_slabs_destroy(h))
+
+
+def hisq_slabs_dslash(h, vin, vout, nrhs: int, parity: int, ms=None):
+    """Decomposed Dslash on canonical device buffers; ms: optional host float64[4] of event times."""
+    _check(load().hisq_slabs_dslash(h, _ptr(vin), _ptr(vout), int(nrhs), int(parity), _ptr(ms)))
 
 
 def hisq_aop_noalloc(fat, naik, mass: float, vin, vout, nrhs: int, pAp=None):
