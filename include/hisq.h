@@ -205,7 +205,9 @@ int hisq_slabs_dslash(hisq_slabs *h, const double *in, double *out, int nrhs, in
  * less 1 MiB of reduction space, e.g. FP32 32^3x8 up to nrhs = 4; larger requests return
  * HISQ_ERR_ARG with a message naming the limit, and nothing is launched.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call shares the
+ * that device current; make that first call before any stream capture.  The address is kept for
+ * the life of the process: it stays valid until the device is reset (cudaDeviceReset tears down
+ * the context that holds the array; do not call this entry point after one).  Every call shares the
  * one array and leaves its contents behind (the block counter is cleared at the start of each
  * call): calls that overlap on the GPU, from several streams or host threads, race. */
 int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, double mass, const void *in,

@@ -330,11 +330,6 @@ LaunchShape default_shape(int prec, int n) {
     return {R, 256, 1};
 }
 
-static int pow2_floor(int x) {
-    int p = 1;
-    while (p * 2 <= x) p *= 2;
-    return p;
-}
 
 int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int copy, const DslashArgs &d,
                   const LaunchShape *shape, cudaStream_t stream, int *grid_out) {
@@ -364,7 +359,6 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     int t = (d.n + R - 1) / R;
     // reducing epilogues finish in one block that sums a partial per block: blocks of at least 128
     // threads keep both the partial count and that block's share of the sum small
-    int want_threads = d.epi != EPI_PLAIN ? std::max(sh.threads, 128) : sh.threads;
     int spb, threads;
     if (S == 8) {
         // staged: threads = 4 t TS exactly (TS sites per tile), up to 512
@@ -372,8 +366,7 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
         threads = 4 * t * spb;
         if (threads % 32) return set_error(HISQ_ERR_ARG, "staged launch shape of %d threads is not whole warps", threads);
     } else {
-        spb = pow2_floor(std::max(1, std::min(want_threads, 256) / (S * t)));  // kernels are bounded to 256 threads
-        threads = (spb * S * t + 31) / 32 * 32;  // whole warps; threads with site index >= spb idle
+        dslash_block_shape(d.n, R, S, sh.threads, d.epi != EPI_PLAIN, &spb, &threads);
         if (threads > 256) return set_error(HISQ_ERR_ARG, "launch shape of %d threads is too large", threads);
     }
 
@@ -425,10 +418,8 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     } else if (d.epi != EPI_PLAIN) {
         size_t need = std::max((size_t)spb * d.n, (size_t)threads + 64);
         smem = need * sizeof(double);
-        long tiles = (a.s1 - a.s0 + spb - 1) / spb;
         // the grid never exceeds one resident wave per SM times 64, nor the tile count
-        size_t max_grid = (size_t)std::min<long>(tiles, (long)ctx->num_sms * 64);
-        if (!d.partials || !d.counter || max_grid * d.n > d.partials_cap)
+        if (!d.partials || !d.counter || dslash_partials_needed(a.s1 - a.s0, ctx->num_sms, spb, d.n) > d.partials_cap)
             return set_error(HISQ_ERR_ARG, "reduction scratch too small for the Dslash epilogue");
     }
     int grid = 0;
@@ -447,7 +438,7 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
 
 static bool valid_prec(int p) { return p >= HISQ_FP64 && p <= HISQ_BF16; }
 
-static int check_pair(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik) {
+int check_pair(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik) {
     if (!fat || !naik) return set_error(HISQ_ERR_ARG, "null links handle");
     if (fat->ctx != ctx || naik->ctx != ctx)
         return set_error(HISQ_ERR_STATE, "links handles belong to another context");

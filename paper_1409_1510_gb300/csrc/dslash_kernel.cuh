@@ -173,6 +173,7 @@ __device__ __forceinline__ void load_neighbours(const VecView<P> &vin, int nb, i
 // provide the same load().
 template <int P, bool COHERENT>
 struct PlainIn {
+    static constexpr bool coherent = COHERENT;
     VecView<P> v;
     template <int R>
     __device__ __forceinline__ void load(int nb, int r0, const bool act[R], Cplx<typename Prec<P>::real> out[R][3]) const {
@@ -187,6 +188,140 @@ __device__ __forceinline__ void scale_acc(Cplx<T> acc[R][3], T f) {
     for (int r = 0; r < R; r++)
 #pragma unroll
         for (int c = 0; c < 3; c++) acc[r][c] = {acc[r][c].re * f, acc[r][c].im * f};
+}
+
+// ---- paired FP32 arithmetic for 16-bit storage and an even number R of right-hand sides ----
+//
+// Two right-hand sides r, r + 1 share every link element, so their real parts (and their
+// imaginary parts) form one float2 and each complex multiply-add of a link element with the two
+// vectors is four packed fused multiply-adds (fma.rn.f32x2, two FP32 lanes per instruction) in
+// place of eight scalar ones: Re w += Re M Re v - Im M Im v is kept as two sums, the second
+// (Im M Im v) in its own accumulator and subtracted once at the end, so no operand is negated.
+// The 16-bit vectors are decoded straight into the pairs and scaled with packed multiplies.
+template <int Q2>
+struct PairAcc {
+    float2 re[Q2][3], im[Q2][3], neg[Q2][3];
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+template <int Q2>
+__device__ __forceinline__ void pair_scale(PairAcc<Q2> &A, float f) {
+    const float2 ff = f2(f, f);
+#pragma unroll
+    for (int q = 0; q < Q2; q++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            A.re[q][c] = __fmul2_rn(A.re[q][c], ff);
+            A.im[q][c] = __fmul2_rn(A.im[q][c], ff);
+            A.neg[q][c] = __fmul2_rn(A.neg[q][c], ff);
+        }
+}
+
+// the pairs (Re v_r, Re v_{r+1}), (Im v_r, Im v_{r+1}) of the neighbour nb for r = r0 + 2q
+template <int P, int Q2, bool COHERENT>
+__device__ __forceinline__ void load_pairs(const void *data, int n, int nb, int r0, const bool act[2 * Q2],
+                                           float2 vr[Q2][3], float2 vi[Q2][3]) {
+    if constexpr (P == HISQ_FP16) {
+        const uint4 *rec = reinterpret_cast<const uint4 *>(data) + (size_t)nb * n + r0;
+#pragma unroll
+        for (int q = 0; q < Q2; q++) {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            const uint4 a = act[2 * q] ? vld<COHERENT>(rec + 2 * q) : z;
+            const uint4 b = act[2 * q + 1] ? vld<COHERENT>(rec + 2 * q + 1) : z;
+            const float2 sc = f2(__uint_as_float(a.w), __uint_as_float(b.w));
+            const uint32_t ha[3] = {a.x, a.y, a.z}, hb[3] = {b.x, b.y, b.z};
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&ha[c]));
+                const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&hb[c]));
+                vr[q][c] = __fmul2_rn(f2(fa.x, fb.x), sc);
+                vi[q][c] = __fmul2_rn(f2(fa.y, fb.y), sc);
+            }
+        }
+    } else {
+        static_assert(P == HISQ_BF16, "paired loads for 16-bit storage");
+        // element (s, c, r) is the bf16 pair (re, im) at (s * 3 + c) n + r: two adjacent right-hand
+        // sides are one 8-byte word; a bf16 is the top half of its float
+        const uint32_t *e = reinterpret_cast<const uint32_t *>(data);
+#pragma unroll
+        for (int q = 0; q < Q2; q++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const size_t idx = ((size_t)nb * 3 + c) * n + r0 + 2 * q;
+                const uint32_t a = act[2 * q] ? vld<COHERENT>(e + idx) : 0u;
+                const uint32_t b = act[2 * q + 1] ? vld<COHERENT>(e + idx + 1) : 0u;
+                vr[q][c] = f2(__uint_as_float(a << 16), __uint_as_float(b << 16));
+                vi[q][c] = f2(__uint_as_float(a & 0xffff0000u), __uint_as_float(b & 0xffff0000u));
+            }
+    }
+}
+
+template <int Q2>
+__device__ __forceinline__ void matvec_pairs(const Cplx<float> M[3][3], const float2 vr[Q2][3], const float2 vi[Q2][3],
+                                             PairAcc<Q2> &A) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const float2 mr = f2(M[a][b].re, M[a][b].re), mi = f2(M[a][b].im, M[a][b].im);
+#pragma unroll
+            for (int q = 0; q < Q2; q++) {
+                A.re[q][a] = __ffma2_rn(mr, vr[q][b], A.re[q][a]);
+                A.neg[q][a] = __ffma2_rn(mi, vi[q][b], A.neg[q][a]);
+                A.im[q][a] = __ffma2_rn(mr, vi[q][b], A.im[q][a]);
+                A.im[q][a] = __ffma2_rn(mi, vr[q][b], A.im[q][a]);
+            }
+        }
+}
+
+// site_stencil for 16-bit 18-real records, R even, S = 1 or 2 (same fields, scales and slots)
+template <int P, int R, int S, bool COHERENT>
+__device__ __forceinline__ void site_stencil_pairs(const Geom &g, const LinkField &fat_f, const LinkField &naik_f,
+                                                   int parity, const void *in, int n, int s, int part, int r0,
+                                                   const bool act[R], Cplx<float> acc[R][3]) {
+    using C = LinkCodec<P, 18>;
+    constexpr int Q2 = R / 2;
+    const SiteCoord sc = decode_site(g, s, parity);
+    const size_t site = (size_t)parity * g.Vh + s;
+    PairAcc<Q2> A;
+#pragma unroll
+    for (int q = 0; q < Q2; q++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) A.re[q][c] = A.im[q][c] = A.neg[q][c] = f2(0.f, 0.f);
+#pragma unroll
+    for (int kind = 0; kind < (S == 1 ? 2 : 1); kind++) {
+        const bool naik_kind = (S == 1) ? (kind == 1) : (part == 1);
+        const LinkField f = naik_kind ? naik_f : fat_f;
+        const int hop = naik_kind ? 3 : 1;
+        if (S == 1 && kind == 1) pair_scale(A, __ldg(fat_f.scale + site) / __ldg(naik_f.scale + site));
+#pragma unroll
+        for (int grp = 0; grp < C::GROUPS; grp++) {
+            uint32_t u[C::WG * 4];
+            C::load_group(f, parity, g.Vh, s, grp, u);
+#pragma unroll
+            for (int l = 0; l < C::G; l++) {
+                const int slot = grp * C::G + l;
+                const int nb = neighbour(g, sc, s, slot >> 1, (slot & 1) ? -hop : hop);
+                Cplx<float> M[3][3];
+                C::decode(u, l, M);
+                float2 vr[Q2][3], vi[Q2][3];
+                load_pairs<P, Q2, COHERENT>(in, n, nb, r0, act, vr, vi);
+                matvec_pairs<Q2>(M, vr, vi, A);
+            }
+        }
+        // S = 1: after the Naik field, acc = s_N (s_X / s_N sum_X + sum_N); S = 2: the lane's field
+        if (S != 1 || kind == 1) pair_scale(A, __ldg(f.scale + site));
+    }
+    const float2 m1 = f2(-1.f, -1.f);
+#pragma unroll
+    for (int q = 0; q < Q2; q++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float2 re = __ffma2_rn(A.neg[q][c], m1, A.re[q][c]);
+            acc[2 * q][c] = {re.x, A.im[q][c].x};
+            acc[2 * q + 1][c] = {re.y, A.im[q][c].y};
+        }
 }
 
 // The stencil of Eq. (3) at output site s (parity `parity`): writes into acc the sum of the
@@ -206,6 +341,10 @@ __device__ __forceinline__ void site_stencil(const Geom &g, const LinkField &fat
     using FatC = LinkCodec<P, 18>;
     using NaikC = LinkCodec<P, NR>;
     constexpr bool SCALED = (P == HISQ_FP16 || P == HISQ_BF16);  // 18-real records of 16-bit fields
+    if constexpr (SCALED && NR == 18 && R % 2 == 0 && (S == 1 || S == 2)) {
+        site_stencil_pairs<P, R, S, IN::coherent>(g, fat_f, naik_f, parity, vin.v.data, vin.v.n, s, part, r0, act, acc);
+        return;
+    }
     const SiteCoord sc = decode_site(g, s, parity);
     const size_t site = (size_t)parity * g.Vh + s;
 #pragma unroll

@@ -401,6 +401,25 @@ struct DslashArgs {
 enum LinkCopy { LINKS_INNER = 0, LINKS_FP64 = 1, LINKS_DS = 2 };
 // the copy that gives FP64 accuracy for these links: double-single unless they are FP64 already
 inline int links_hp(const hisq_links *fat) { return fat->residual_ds() ? LINKS_DS : LINKS_FP64; }
+// Sites per block and threads per block of a (non-staged) Dslash launch of n right-hand sides,
+// R per thread and S lanes per site, for the shape's block size (reducing epilogues use at
+// least 128 threads); launch_dslash and every caller that sizes reduction scratch in advance use it
+inline void dslash_block_shape(int n, int R, int S, int shape_threads, bool reducing, int *spb, int *threads) {
+    const int t = (n + R - 1) / R;
+    const int want = reducing ? std::max(shape_threads, 128) : shape_threads;
+    int p = 1;
+    while (p * 2 <= std::max(1, std::min(want, 256) / (S * t))) p *= 2;  // kernels are bounded to 256 threads
+    *spb = p;
+    *threads = (p * S * t + 31) / 32 * 32;  // whole warps; threads with site index >= spb idle
+}
+// the reduction partials (doubles) a reducing Dslash epilogue of that shape writes on a parity of
+// Vh sites: one per block and right-hand side, the grid capped at 64 blocks per SM
+inline size_t dslash_partials_needed(long Vh, int num_sms, int spb, int n) {
+    const long tiles = (Vh + spb - 1) / spb;
+    return (size_t)std::min<long>(tiles, (long)num_sms * 64) * n;
+}
+// (fat, naik) handles of this context with matching precisions (context.cu)
+int check_pair(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik);
 // grid_out (optional) receives the number of blocks launched (= partials written per dot)
 int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, int copy,
                   const DslashArgs &a, const LaunchShape *shape, cudaStream_t stream, int *grid_out = nullptr);

@@ -38,12 +38,6 @@ static int scratch_address(int device, unsigned char **out) {
     return HISQ_OK;
 }
 
-static int pow2_floor_na(int x) {
-    int p = 1;
-    while (p * 2 <= x) p *= 2;
-    return p;
-}
-
 }  // namespace hisq
 
 using namespace hisq;
@@ -52,10 +46,7 @@ extern "C" int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, d
                                 int nrhs, double *pAp) {
     hisq_ctx *ctx;
     HISQ_CHECK(require_ctx(&ctx));
-    if (!fat || !naik) return set_error(HISQ_ERR_ARG, "null links handle");
-    if (fat->ctx != ctx || naik->ctx != ctx) return set_error(HISQ_ERR_STATE, "links handles belong to another context");
-    if (fat->is_naik || !naik->is_naik) return set_error(HISQ_ERR_ARG, "expected (fat, naik) links handles");
-    if (fat->prec != naik->prec) return set_error(HISQ_ERR_ARG, "fat and Naik links have different precisions");
+    HISQ_CHECK(check_pair(ctx, fat, naik));
     if (!in || !out) return set_error(HISQ_ERR_ARG, "null vector");
     if (in == out) return set_error(HISQ_ERR_ARG, "in and out must not overlap");
     if (nrhs < 1 || nrhs > HISQ_MAX_NRHS) return set_error(HISQ_ERR_ARG, "nrhs must be in 1..%d", HISQ_MAX_NRHS);
@@ -68,10 +59,11 @@ extern "C" int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, d
                          "hisq_aop_noalloc: the odd-parity intermediate needs %zu bytes, more than the %zu bytes of "
                          "static scratch (HISQ_AOP_NOALLOC_SCRATCH_BYTES); use hisq_aop",
                          tmp_bytes, NOALLOC_TMP_BYTES);
-    const int t = nrhs / shape.R;
-    const int spb = pow2_floor_na(std::max(1, std::min(shape.threads, 256) / t));
-    const long tiles = (ctx->geom.Vh + spb - 1) / spb;
-    const size_t partials = (size_t)std::min<long>(tiles, (long)ctx->num_sms * 64) * nrhs;
+    // the partials the reducing launch will write, sized by the helper launch_dslash itself uses,
+    // so a request is rejected before anything is launched
+    int spb = 0, threads = 0;
+    dslash_block_shape(nrhs, shape.R, shape.S, shape.threads, true, &spb, &threads);
+    const size_t partials = dslash_partials_needed(ctx->geom.Vh, ctx->num_sms, spb, nrhs);
     if (partials > NOALLOC_PARTIALS_DOUBLES)
         return set_error(HISQ_ERR_ARG,
                          "hisq_aop_noalloc: %zu reduction partials exceed the %zu of the static scratch; use hisq_aop",

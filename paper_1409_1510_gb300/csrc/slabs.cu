@@ -76,9 +76,10 @@ __global__ void slab_gather_kernel(Geom g, Geom gs, int t0, int p, const void *i
     }
 }
 
-// The face-pack kernel: the three outgoing planes at the low end (ts = 4..6) and at the high end
-// (ts = Lts + 1 .. Lts + 3) of the input bundle into the send buffer [low face][high face], each
-// face `face_words` 16-byte words long (3 planes of one parity, every right-hand side).
+// The face-pack kernel: the three outgoing planes at the low end (ts = 4..6, from word low_word)
+// and at the high end (ts = Lts + 1 .. Lts + 3, from word high_word) of the input bundle into the
+// send buffer [low face][high face], each face `face_words` 16-byte words long (3 planes of one
+// parity, every right-hand side).
 __global__ void slab_pack_faces_kernel(const uint4 *in, uint4 *send, long low_word, long high_word, long face_words) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 2 * face_words; i += (long)gridDim.x * blockDim.x)
         send[i] = in[(i < face_words ? low_word : high_word - face_words) + i];
@@ -248,7 +249,7 @@ int hisq_slabs_dslash(hisq_slabs *h, const double *in, double *out, int nrhs, in
         const int blocks = (int)std::min<long>((2 * face_words + 255) / 256, (long)ctx->num_sms * 8);
         slab_pack_faces_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4 *>(h->s[k].in),
                                                        reinterpret_cast<uint4 *>(h->s[k].send), 4 * plane_words,
-                                                       (long)(Lts + 4) * plane_words, face_words);
+                                                       (long)(Lts + 1) * plane_words, face_words);
     }
     HISQ_CUDA(cudaGetLastError());
     HISQ_CUDA(cudaEventRecord(h->ev[0], st));

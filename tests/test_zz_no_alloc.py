@@ -16,7 +16,7 @@ from gpu_util import PREC_TOL, gpu, rel_err
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,n", [(1, 1), (1, 4), (2, 3)])
+@pytest.mark.parametrize("prec,n", [(1, 1), (1, 4), (2, 3), (0, 2), (3, 4)])
 def test_noalloc_matches_aop_twice(prec, n):
     mass = 0.1
     with gpu((8, 10, 8, 6), prec) as g:
@@ -40,3 +40,19 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch():
         vin, out = g.bundle(n), g.bundle(n)
         with pytest.raises(hisq.HisqError, match="static scratch"):
             g.hisq.hisq_aop_noalloc(g.fat, g.naik, 0.1, vin, out, n)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_noalloc_first_call_on_a_fresh_context_matches_oracle(prec):
+    """The first operator call of a new context goes through the static scratch (hisq_aop has not
+    run, so no workspace exists yet) and equals the oracle's A = m^2 - D_eo D_oe."""
+    mass = 0.1
+    with gpu((8, 8, 8, 6), prec) as g:
+        v = np.stack([hi.gaussian_rhs(g.lat, 30 + k) for k in range(2)])
+        out = g.bundle(2)
+        pap = np.zeros(2)
+        g.hisq.hisq_aop_noalloc(g.fat, g.naik, mass, g.pack(v), out, 2, pap)
+        want = np.stack([g.oracle.aop(v[k], mass) for k in range(2)])
+        assert rel_err(g.unpack(out, 2), want) <= 2 * PREC_TOL[prec]
+        pap_want = np.array([np.vdot(v[k], want[k]).real for k in range(2)])
+        assert np.max(np.abs(pap - pap_want) / np.abs(pap_want)) <= 4 * PREC_TOL[prec]
