@@ -69,25 +69,17 @@ static int run_tuner(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *nai
     const int Ts[] = {256, 128, 64, 32};
     int rc = HISQ_OK;
     const int recon = copy != LINKS_INNER ? 18 : naik->recon;
-    const int words = link_words(prec, 18) + link_words(prec, recon);
     for (int R : Rs) {
         if (n % R != 0) continue;
         if (prec == HISQ_FP64 && R > 4) continue;
         if (prec == HISQ_DS && R > 2) continue;  // double-single: one or two RHS per thread, no lane split
-        for (int S = 1; S <= 8; S *= 2) {
+        // the staged variant (S = 8) is not a candidate: it was slower than the plain kernel at every
+        // size measured (it stays available through hisq_set_launch_shape)
+        for (int S = 1; S <= 4; S *= 2) {
         if (S > 1 && prec == HISQ_DS) continue;
-        if (S > 1 && (recon != 18 || R > 8 / std::min(S, 4))) continue;
-        if (S == 8 && (prec == HISQ_FP64 || R > 2)) continue;
+        if (S > 1 && (recon != 18 || R > 8 / S)) continue;
         for (int T : Ts) {
             LaunchShape sh{R, T, S};
-            if (S == 8) {
-                // staged: sites per tile 32 T / 256 (32..256) times 4 t lanes, within one block
-                const int t = n / R, TS = T / 2;
-                sh.threads = 4 * t * TS;
-                if (sh.threads > 512 || sh.threads % 32 ||
-                    staged_smem(words, TS, sh.threads, n, false) > 200 * 1024)
-                    continue;
-            }
             float ms = 0;
             rc = time_shape(ctx, fat, naik, copy, n, sh, in, out, flush, flush_bytes, &ms);
             if (rc != HISQ_OK) break;
