@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--dims", default=None)
     ap.add_argument("--mass", type=float, default=None)
     ap.add_argument("--step-rhs", type=int, default=16, help="cg: right-hand sides solved per step")
+    ap.add_argument("--bundle", type=int, default=16,
+                    help="cg: right-hand sides per bundle (0: chosen by the autotuner from the Dslash timings)")
     ap.add_argument("--rhs", default="z2", choices=["z2", "gaussian"], help="cg: kind of right-hand side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -69,6 +71,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--nrhs", type=int, default=1500, help="production: right-hand sides in the sweep")
     ap.add_argument("--pc", action="store_true", help="production: also train and apply the network")
+    ap.add_argument("--recon", type=int, default=18, choices=[18, 13, 9],
+                    help="dslash: reals stored per Naik link (13 and 9: reconstructed from SU(3) times a scale)")
     ap.add_argument("--shape", default=None,
                     help="dslash: launch shape R,threads,lanes (skips the autotuner, so that the only "
                          "Dslash launches are one warm-up and the --steps timed ones)")
@@ -87,7 +91,8 @@ def workload(args):
     kind = "Z2-noise" if args.rhs == "z2" else "Gaussian"
     return dims, {
         "workload": f"{'x'.join(map(str, dims[:3]))}x{dims[3]} even-odd HISQ CG on m^2 - D_eo D_oe, m={args.mass}, "
-                    f"{n} {kind} RHS per step in autotuned bundles sharing every link read, {args.inner} storage / "
+                    f"{n} {kind} RHS per step in bundles of {args.bundle or 'autotuned size'} sharing every link "
+                    f"read, {args.inner} storage / "
                     f"fp32 arithmetic, FP64-accurate reliable updates (delta 0.1, double-single arithmetic on the "
                     f"FP32 pipe), FP64 true residual <= 1e-10 per RHS",
         "lattice": dims, "rhs_per_step": n, "rhs": kind, "mass": args.mass, "inner_storage": args.inner,
@@ -370,7 +375,7 @@ def small_lattice_figures(hisq, torch, hi, inner, stream, dev, flush):
         out["speedup_vs_fp64_cg"] = out["fp64"]["ms_per_rhs"] / out["mixed"]["ms_per_rhs"]
         bs = [d64(hi.gaussian_rhs(lat, 100 + k)) for k in range(16)]
         xs = [torch.zeros_like(v) for v in bs]
-        set_params(hisq, inner, 2, 0)
+        set_params(hisq, inner, 2, 0, 16)
         solve_ms(hisq, torch, stream, fat, naik, bs, xs, SMALL_MASS, flush)
         bms = [solve_ms(hisq, torch, stream, fat, naik, bs, xs, SMALL_MASS, flush)[0] for _ in range(3)]
         out["bundle_of_16"] = {"ms_per_rhs": statistics.median(bms) / 16,
@@ -414,8 +419,8 @@ def run_ours(args, rank, world, local_rank, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up: tunes the Dslash launch shapes and the bundle size, first launches
-    set_params(hisq, inner, 2, 1)
+    # warm-up: tunes the Dslash launch shapes (and the bundle size with --bundle 0), first launches
+    set_params(hisq, inner, 2, 1, args.bundle)
     for _ in range(args.warmup):
         solve_ms(hisq, torch, stream, fat, naik, bs, xs, mass, flush)
 
@@ -518,7 +523,7 @@ def run_ours(args, rank, world, local_rank, dist):
         # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region) ----
         bh = [torch.from_numpy(np.ascontiguousarray(v).view(np.float64).copy()).pin_memory() for v in rhs_host]
         xh = [torch.empty_like(v).pin_memory() for v in bh]
-        set_params(hisq, inner, 2, 0)
+        set_params(hisq, inner, 2, 0, args.bundle)
         hisq.hisq_cg_solve(fat, naik, bh, xh, mass, TOL)
         ke = max(2, min(args.steps, 4))
         el, est = [], []
@@ -627,13 +632,13 @@ def run_dslash(args):
     d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
     prec = PREC[args.inner] if args.inner in PREC else 2
     fat = hisq.hisq_links_create(d64(X), False, prec, 18)
-    naik = hisq.hisq_links_create(d64(N), True, prec, 18)
+    naik = hisq.hisq_links_create(d64(N), True, prec, args.recon)
     vin = torch.empty(hisq.hisq_vector_bytes(prec, n), dtype=torch.uint8, device=dev)
     hisq.hisq_pack(d64(np.stack([hi.gaussian_rhs(lat, k) for k in range(n)])), vin, n, prec)
     vout = torch.empty_like(vin)
     if args.shape:
         shape = tuple(int(v) for v in args.shape.split(","))
-        hisq.hisq_set_launch_shape(prec, 18, n, *shape)
+        hisq.hisq_set_launch_shape(prec, args.recon, n, *shape)
     else:
         shape = hisq.hisq_autotune(fat, naik, n)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -649,10 +654,12 @@ def run_dslash(args):
         ts.append(e0.elapsed_time(e1))
     sec = statistics.median(ts) / 1e3
     elem = {0: 8, 1: 4, 2: 2, 3: 2}[prec]
-    byts = acc.compulsory_bytes(n, elem, elem, 18, 8.0 if prec in (2, 3) else 0.0, 4.0 if prec == 2 else 0.0) \
-        * lat.half_volume
+    # 16-bit records carry a float scale per site for the fat field, and for the Naik field when stored in full
+    scales = (4.0 * (1 + (args.recon == 18))) if prec in (2, 3) else 0.0
+    byts = acc.compulsory_bytes(n, elem, elem, args.recon, scales, 4.0 if prec == 2 else 0.0) * lat.half_volume
     hbm_peak, _ = peaks()
-    print(json.dumps({"mode": "dslash", "lattice": dims, "precision": args.inner, "nrhs": n, "launches": args.steps,
+    print(json.dumps({"mode": "dslash", "lattice": dims, "precision": args.inner, "naik_reals": args.recon,
+                      "nrhs": n, "launches": args.steps,
                       "us": sec * 1e6, "gflops": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e9,
                       "gbs": byts / sec / 1e9, "frac_hbm": byts / sec / 1e9 / hbm_peak,
                       "shape_arg": ",".join(str(v) for v in shape)}), flush=True)
@@ -867,8 +874,12 @@ def run_batch(args):
         for name, driver in (("persistent", 2), ("graph", 1)):
             _solve_set(hisq, torch, fat, naik, bs[:n], mass, inner_prec=1, bundle=n, use_graph=driver)  # warm-up
             sec, st, iters, res = _solve_set(hisq, torch, fat, naik, bs, mass, inner_prec=1, bundle=n, use_graph=driver)
+            # right-hand-side iterations a bundle's Dslash phases spend on converged (masked) lanes
+            idle = sum(int(iters[k0:k0 + n].max()) * len(iters[k0:k0 + n]) - int(iters[k0:k0 + n].sum())
+                       for k0 in range(0, nrhs, n))
             row[name] = {"s_per_rhs": sec / nrhs, "iterations_min": int(iters.min()), "iterations_max": int(iters.max()),
-                         "bundle_iterations": int(st.bundle_iterations), "converged": int(st.converged),
+                         "iterations_sum": int(iters.sum()), "bundle_iterations": int(st.bundle_iterations),
+                         "masked_lane_fraction": idle / (idle + int(iters.sum())), "converged": int(st.converged),
                          "max_true_residual": float(res.max())}
         rows.append(row)
         print(json.dumps(row), flush=True)

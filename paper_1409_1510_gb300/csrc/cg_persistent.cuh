@@ -304,8 +304,9 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
     const int ts = tile_sites(g.Vh, spb);
     if (any && sl < ts) {
         for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
-            const int s = tile * ts + sl;
-            if (s >= g.Vh) break;
+            const int q = tile * ts + sl;
+            if (q >= g.Vh) break;
+            const int s = visit_site(g, q);
             Cplx<real> acc[R][3];
             // 16-bit storage: the epilogue's own record (one 16-byte word per site and RHS) is
             // requested before the stencil, so its L2 latency overlaps the link and neighbour
@@ -381,51 +382,67 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
 }
 
 // The FP64-accurate residual recomputation of a mixed-precision solve in double-single
-// arithmetic (ds_arith.cuh) over the block's share of the sites, one thread per (site, listed
-// right-hand side list[i], i < nlist).  EPI_PLAIN: out = D in (ds bundles).  EPI_RESID:
-// r = b - m^2 x + D in with x, b FP64 and an FP64 epilogue, written to out_lo in the iterated
-// precision Q, with |r|^2 per block published as column i of the list.
-template <int EPI, int Q>
+// arithmetic (ds_arith.cuh) over the block's share of the sites, one thread per site and DR
+// listed right-hand sides list[DR gi .. DR gi + DR) (nlist listed in all).  The solver uses
+// DR = 1: two right-hand sides per thread, which share each link load and give a thread two
+// independent accumulation chains, measured no faster at 64^3 x 16 with 16 right-hand sides.
+// EPI_PLAIN: out = D in (ds bundles).  EPI_RESID: r = b - m^2 x + D in with x, b FP64
+// and an FP64 epilogue, written to out_lo in the iterated precision Q, with |r|^2 per block
+// published as column i of the list.
+template <int EPI, int Q, int DR>
 __device__ __forceinline__ void ds_phase(const PersArgs &a, const void *in, void *out, int parity, const void *xvec,
                                          const void *bvec, void *out_lo, double *red, const double *m2v,
                                          const int *list, int nlist) {
     const Geom &g = a.g;
-    const int n = a.n, t = nlist, spb = blockDim.x / t;
-    const int tid = threadIdx.x, gi = tid % t, sl = tid / t, r0 = list[gi];
-    const bool act[1] = {true};
-    double dot[1] = {0.0};
+    const int n = a.n, t = (nlist + DR - 1) / DR, spb = blockDim.x / t;
+    const int tid = threadIdx.x, gi = tid % t, sl = tid / t;
+    bool act[DR];
+    int rr[DR];
+#pragma unroll
+    for (int r = 0; r < DR; r++) {
+        act[r] = DR * gi + r < nlist;
+        rr[r] = act[r] ? list[DR * gi + r] : 0;
+    }
+    double dot[DR];
+#pragma unroll
+    for (int r = 0; r < DR; r++) dot[r] = 0.0;
     const int ts = tile_sites(g.Vh, spb);
     if (sl < ts) {
         for (int tile = blockIdx.x; (long)tile * ts < g.Vh; tile += gridDim.x) {
-            const int s = tile * ts + sl;
-            if (s >= g.Vh) break;
-            dscplx acc[1][3];
-            ds_site_stencil<1, true>(g, a.fat64, a.naik64, parity, reinterpret_cast<const float4 *>(in), n, s, r0, act,
-                                     acc);
-            if constexpr (EPI == EPI_PLAIN) {
-                ds_store3(reinterpret_cast<float4 *>(out), n, s, r0, acc[0]);
-            } else {
-                static_assert(EPI == EPI_RESID, "the double-single phases are D in and the residual");
-                const double m2 = m2v[r0];
-                const double2 *vx = reinterpret_cast<const double2 *>(xvec);
-                const double2 *vb = reinterpret_cast<const double2 *>(bvec);
-                Cplx<typename Prec<Q>::real> lo3[3];
-                double d = 0.0;
+            const int q = tile * ts + sl;
+            if (q >= g.Vh) break;
+            const int s = visit_site(g, q);
+            dscplx acc[DR][3];
+            ds_site_stencil<DR, true>(g, a.fat64, a.naik64, parity, reinterpret_cast<const float4 *>(in), n, s, rr, act,
+                                      acc);
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const long idx = ((long)s * 3 + c) * n + r0;
-                    const double2 x = __ldcg(vx + idx), b = __ldcg(vb + idx);
-                    const double wr = b.x - m2 * x.x + ds_value(acc[0][c].re);
-                    const double wi = b.y - m2 * x.y + ds_value(acc[0][c].im);
-                    d += wr * wr + wi * wi;
-                    lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+            for (int r = 0; r < DR; r++) {
+                if (!act[r]) continue;
+                if constexpr (EPI == EPI_PLAIN) {
+                    ds_store3(reinterpret_cast<float4 *>(out), n, s, rr[r], acc[r]);
+                } else {
+                    static_assert(EPI == EPI_RESID, "the double-single phases are D in and the residual");
+                    const double m2 = m2v[rr[r]];
+                    const double2 *vx = reinterpret_cast<const double2 *>(xvec);
+                    const double2 *vb = reinterpret_cast<const double2 *>(bvec);
+                    Cplx<typename Prec<Q>::real> lo3[3];
+                    double d = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const long idx = ((long)s * 3 + c) * n + rr[r];
+                        const double2 x = __ldcg(vx + idx), b = __ldcg(vb + idx);
+                        const double wr = b.x - m2 * x.x + ds_value(acc[r][c].re);
+                        const double wi = b.y - m2 * x.y + ds_value(acc[r][c].im);
+                        d += wr * wr + wi * wi;
+                        lo3[c] = {(typename Prec<Q>::real)wr, (typename Prec<Q>::real)wi};
+                    }
+                    dot[r] += d;
+                    store_vec<Q>(VecView<Q>{out_lo, n}, s, rr[r], lo3);
                 }
-                dot[0] += d;
-                store_vec<Q>(VecView<Q>{out_lo, n}, s, r0, lo3);
             }
         }
     }
-    if constexpr (EPI == EPI_RESID) publish_dots<1>(a, red, dot, t, gi, nlist);
+    if constexpr (EPI == EPI_RESID) publish_dots<DR>(a, red, dot, t, gi, nlist);
 }
 
 // x_hi of one site and right-hand side, written in double-single form for the recomputation

@@ -514,6 +514,7 @@ int hisq_init(const int dims[4], int device, void *cuda_stream) {
     g.stride[1] = g.half;
     g.stride[2] = g.half * dims[1];
     g.stride[3] = g.half * dims[1] * dims[2];
+    g.plane_order = dims[3] < dims[2] ? 1 : 0;
     ctx->device = device;
     ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaDeviceProp prop;

@@ -91,13 +91,13 @@ __device__ __forceinline__ void ds_row_acc(const uint4 m[3], const float4 v[3], 
     }
 }
 
-// The stencil of Eq. (3) at output site s of parity `parity` in ds arithmetic for R right-hand
-// sides r0 + j of the ds input bundle `in` (n right-hand sides): the 8 fat and 8 Naik links of the
-// site's gathered ds records (slot 2 mu forward, 2 mu + 1 the backward -U^dagger, as in every
-// other precision) times the neighbouring input vectors, summed into acc.
+// The stencil of Eq. (3) at output site s of parity `parity` in ds arithmetic for the R
+// right-hand sides rr[0..R) of the ds input bundle `in` (n right-hand sides): the 8 fat and 8 Naik
+// links of the site's gathered ds records (slot 2 mu forward, 2 mu + 1 the backward -U^dagger, as
+// in every other precision) times the neighbouring input vectors, summed into acc.
 template <int R, bool COHERENT>
 __device__ __forceinline__ void ds_site_stencil(const Geom &g, const LinkField &fat, const LinkField &naik, int parity,
-                                                const float4 *in, int n, int s, int r0, const bool act[R],
+                                                const float4 *in, int n, int s, const int rr[R], const bool act[R],
                                                 dscplx acc[R][3]) {
     const SiteCoord sc = decode_site(g, s, parity);
 #pragma unroll
@@ -118,7 +118,7 @@ __device__ __forceinline__ void ds_site_stencil(const Geom &g, const LinkField &
             for (int r = 0; r < R; r++)
 #pragma unroll
                 for (int c = 0; c < 3; c++)
-                    v[r][c] = act[r] ? ds_load<COHERENT>(in, ((long)nb * 3 + c) * n + r0 + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[r][c] = act[r] ? ds_load<COHERENT>(in, ((long)nb * 3 + c) * n + rr[r]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 uint4 m[3];

@@ -43,11 +43,16 @@ __global__ void __launch_bounds__(256) dslash_ds_kernel(KArgs a) {
 #pragma unroll
     for (int r = 0; r < R; r++) dot[r] = 0.0;
 
+    const bool whole = a.s0 == 0 && a.s1 == g.Vh;  // a whole parity: visit in plane order
     for (int tile = blockIdx.x; (long)tile * a.spb < a.s1 - a.s0; tile += gridDim.x) {
-        const int s = a.s0 + tile * a.spb + sl;
-        if (!(sl < a.spb && s < a.s1 && any_act)) continue;
+        const int q = tile * a.spb + sl;
+        if (!(sl < a.spb && q < a.s1 - a.s0 && any_act)) continue;
+        const int s = whole ? visit_site(g, q) : a.s0 + q;
         dscplx acc[R][3];
-        ds_site_stencil<R, false>(g, a.fat, a.naik, a.parity, in, a.n, s, r0, act, acc);
+        int rr[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) rr[r] = r0 + r;
+        ds_site_stencil<R, false>(g, a.fat, a.naik, a.parity, in, a.n, s, rr, act, acc);
         if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
             for (int r = 0; r < R; r++)

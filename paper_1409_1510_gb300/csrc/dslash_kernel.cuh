@@ -464,9 +464,11 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
 #pragma unroll
     for (int r = 0; r < R; r++) dot[r] = 0.0;
 
+    const bool whole = a.s0 == 0 && a.s1 == g.Vh;  // a whole parity: visit in plane order
     for (int tile = blockIdx.x; (long)tile * a.spb < a.s1 - a.s0; tile += gridDim.x) {
-        const int s = a.s0 + tile * a.spb + sl;
-        const bool valid = sl < a.spb && s < a.s1 && any_act;
+        const int q = tile * a.spb + sl;
+        const bool valid = sl < a.spb && q < a.s1 - a.s0 && any_act;
+        const int s = whole ? visit_site(g, valid ? q : 0) : a.s0 + q;
         if (S == 1 && !valid) continue;
 
         Cplx<real> acc[R][3];

@@ -44,6 +44,7 @@ struct Geom {
     int half;      // Lx / 2
     int Vh;        // V / 2
     int stride[4]; // even-odd index stride of one step in y, z, t (stride[0] unused)
+    int plane_order;  // 1: stencil passes visit the xy-planes with t varying before z (visit_site)
 };
 
 struct SiteCoord {
@@ -64,7 +65,24 @@ __host__ __device__ __forceinline__ SiteCoord decode_site(const Geom &g, int s, 
     return sc;
 }
 
-// even-odd index of the neighbour `step` hops (|step| <= 3 < L) away in direction mu
+// Site of one parity visited at position q of a stencil pass over the whole parity.  The
+// even-odd index runs x fastest, then y, z, t, so a site's +-1 and +-3 neighbours in t are 1 and 3
+// time planes away (Lx Ly Lz / 2 sites each): while a pass sweeps the lattice in that order, the
+// vectors it read at a site's t-neighbours must stay in L2 for three planes of links and vectors,
+// more than the 129 MB of L2 once a bundle of right-hand sides fills GBs.  With plane_order set
+// (t shorter than z) the pass visits the xy-planes (fixed z, t: Lx Ly / 2 consecutive sites) with
+// t varying before z, so t-neighbours are a few xy-planes apart in the visit and z-neighbours
+// 3 Lt xy-planes apart, a quarter of the distance at 64^3 x 16.  Only the order of the visit
+// changes; every site is still computed once.
+__host__ __device__ __forceinline__ int visit_site(const Geom &g, int q) {
+    if (!g.plane_order) return q;
+    const int P = g.stride[2];                 // sites of one xy-plane
+    const int plane = q / P, within = q - plane * P;
+    const int z = plane / g.L[3], t = plane - z * g.L[3];
+    return within + P * (z + g.L[2] * t);
+}
+
+// even-odd index of the neighbour `step` hops (|step| <= 3 < L) away in direction mu// even-odd index of the neighbour `step` hops (|step| <= 3 < L) away in direction mu
 __host__ __device__ __forceinline__ int neighbour(const Geom &g, const SiteCoord &sc, int s, int mu, int step) {
     int c = sc.c[mu] + step;
     int L = g.L[mu];

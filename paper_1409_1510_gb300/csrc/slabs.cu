@@ -158,6 +158,7 @@ int hisq_slabs_create(hisq_slabs **out, const double *fat, const double *naik, i
     g = G;
     g.L[3] = h->Lts + 8;
     g.Vh = h->phv * g.L[3];
+    g.plane_order = 0;  // slab passes cover ranges of time planes in index order
     h->cap_n = 0;
     h->fat_h.ctx = h->naik_h.ctx = ctx;
     h->fat_h.prec = h->naik_h.prec = prec;
