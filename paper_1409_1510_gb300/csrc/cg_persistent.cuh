@@ -386,10 +386,12 @@ __device__ __forceinline__ void dslash_phase(const PersArgs &a, const LinkField 
 // listed right-hand sides list[DR gi .. DR gi + DR) (nlist listed in all).  The solver uses
 // DR = 1: two right-hand sides per thread, which share each link load and give a thread two
 // independent accumulation chains, measured no faster at 64^3 x 16 with 16 right-hand sides.
+// PF: prefetch the next link's operands (it made the persistent kernels spill, so they pass
+// false; the separate kernels of dslash_ds.cu prefetch).
 // EPI_PLAIN: out = D in (ds bundles).  EPI_RESID: r = b - m^2 x + D in with x, b FP64
 // and an FP64 epilogue, written to out_lo in the iterated precision Q, with |r|^2 per block
 // published as column i of the list.
-template <int EPI, int Q, int DR>
+template <int EPI, int Q, int DR, bool PF>
 __device__ __forceinline__ void ds_phase(const PersArgs &a, const void *in, void *out, int parity, const void *xvec,
                                          const void *bvec, void *out_lo, double *red, const double *m2v,
                                          const int *list, int nlist) {
@@ -413,8 +415,8 @@ __device__ __forceinline__ void ds_phase(const PersArgs &a, const void *in, void
             if (q >= g.Vh) break;
             const int s = visit_site(g, q);
             dscplx acc[DR][3];
-            ds_site_stencil<DR, true>(g, a.fat64, a.naik64, parity, reinterpret_cast<const float4 *>(in), n, s, rr, act,
-                                      acc);
+            ds_site_stencil<DR, true, PF>(g, a.fat64, a.naik64, parity, reinterpret_cast<const float4 *>(in), n, s, rr,
+                                          act, acc);
 #pragma unroll
             for (int r = 0; r < DR; r++) {
                 if (!act[r]) continue;

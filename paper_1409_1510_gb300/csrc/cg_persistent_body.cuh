@@ -151,9 +151,9 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
                                                          nullptr, 0, st.update, PlainIn<HISQ_FP64, true>{V64(xhi)}, a.b,
                                                          a.r, red, st.mass2, upd_list, upd_n);
             } else {
-                ds_phase<EPI_PLAIN, Q, 1>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
+                ds_phase<EPI_PLAIN, Q, 1, false>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
                 if (!(ok = grid_sync(a))) break;
-                ds_phase<EPI_RESID, Q, 1>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
+                ds_phase<EPI_RESID, Q, 1, false>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
             }
             if (!(ok = grid_sync(a))) break;
             sum_partials(a, red, upd_n, dots);
@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(pers_threads(R), 1) cg_persistent_kernel(const
                     upd_n = u;
                 }
                 __syncthreads();
-                ds_phase<EPI_PLAIN, Q, 1>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
+                ds_phase<EPI_PLAIN, Q, 1, false>(a, a.xds, a.t64, 1, nullptr, nullptr, nullptr, red, st.mass2, upd_list, upd_n);
                 if (!(ok = grid_sync(a))) break;
-                ds_phase<EPI_RESID, Q, 1>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
+                ds_phase<EPI_RESID, Q, 1, false>(a, a.t64, nullptr, 0, a.xhi, a.b, a.r, red, st.mass2, upd_list, upd_n);
                 if (!(ok = grid_sync(a))) break;
                 sum_partials(a, red, upd_n, dots);
                 if (tid == 0)

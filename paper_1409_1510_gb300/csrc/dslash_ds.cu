@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) dslash_ds_kernel(KArgs a) {
         int rr[R];
 #pragma unroll
         for (int r = 0; r < R; r++) rr[r] = r0 + r;
-        ds_site_stencil<R, false>(g, a.fat, a.naik, a.parity, in, a.n, s, rr, act, acc);
+        ds_site_stencil<R, false, true>(g, a.fat, a.naik, a.parity, in, a.n, s, rr, act, acc);
         if constexpr (EPI == EPI_PLAIN) {
 #pragma unroll
             for (int r = 0; r < R; r++)
