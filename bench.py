@@ -37,7 +37,8 @@ TOL = 1e-10
 MODE_DEFAULTS = {"cg": ("64,64,64,16", 0.002), "production": ("64,64,64,16", 0.002),
                  "batch": ("48,48,48,12", 0.002), "learned": ("32,32,32,8", 0.005),
                  "sweep": ("32,32,32,8", 0.01), "multishift": ("32,32,32,8", 0.01),
-                 "trace": ("32,32,32,8", 0.01), "dslash": ("32,32,32,8", 0.01)}
+                 "trace": ("32,32,32,8", 0.01), "dslash": ("32,32,32,8", 0.01), "slabs": ("64,64,64,16", 0.002)}
+DEFAULT_DELTA = {"fp32": 0.01, "fp16": 0.03, "bf16": 0.1}  # the library's reliable-update threshold by storage
 SMALL_DIMS, SMALL_MASS = (32, 32, 32, 8), 0.01   # the single-RHS precision-form solve (extra keys)
 
 
@@ -58,14 +59,16 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="cg: only the timed region and its roofline (no comparators, no small lattice)")
     ap.add_argument("--mode", default="cg",
-                    choices=["cg", "sweep", "learned", "batch", "production", "multishift", "trace", "dslash"],
+                    choices=["cg", "sweep", "learned", "batch", "production", "multishift", "trace", "dslash",
+                             "slabs"],
                     help="cg: the benchmark line; sweep: Dslash throughput against the number of "
                          "right-hand sides; learned: the learned-preconditioner workload (32^3 x 8); "
                          "batch: bundles with uneven convergence (48^3 x 12); production: a sweep of "
                          "Z2-noise right-hand sides (64^3 x 16); multishift: eight shifted systems "
                          "from one multi-shift solve against separate solves (32^3 x 8); trace: the "
                          "stochastic Tr A^-1 of Eq. (2) from Z2 noise (32^3 x 8); dslash: one Dslash "
-                         "configuration (--inner, --nrhs, --dims) launched --steps times (for profiling)")
+                         "configuration (--inner, --nrhs, --dims) launched --steps times (for profiling); slabs: the "
+                         "Dslash decomposed into t-slabs with depth-3 halos against the undecomposed one")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--test-rhs", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=30)
@@ -93,7 +96,7 @@ def workload(args):
         "workload": f"{'x'.join(map(str, dims[:3]))}x{dims[3]} even-odd HISQ CG on m^2 - D_eo D_oe, m={args.mass}, "
                     f"{n} {kind} RHS per step in bundles of {args.bundle or 'autotuned size'} sharing every link "
                     f"read, {args.inner} storage / "
-                    f"fp32 arithmetic, FP64-accurate reliable updates (delta 0.1, double-single arithmetic on the "
+                    f"fp32 arithmetic, FP64-accurate reliable updates (delta {DEFAULT_DELTA.get(args.inner)}, double-single arithmetic on the "
                     f"FP32 pipe), FP64 true residual <= 1e-10 per RHS",
         "lattice": dims, "rhs_per_step": n, "rhs": kind, "mass": args.mass, "inner_storage": args.inner,
         "fields": "synthetic SU(3) fat links (eps 0.3, 5% noise) and Naik links, staggered phases and "
@@ -337,7 +340,7 @@ def dslash_rate(hisq, torch, hi, lat, fat, naik, prec, n, flush, stream, dev, d6
 def set_params(hisq, prec, driver=2, timing=0, bundle=0):
     # driver: 0 host-driven (CUDA events on every Dslash), 1 CUDA graph, 2 persistent kernel
     p = hisq.hisq_default_solver_params()
-    p.inner_prec, p.use_graph, p.time_kernels, p.delta, p.bundle = prec, driver, timing, 0.1, bundle
+    p.inner_prec, p.use_graph, p.time_kernels, p.bundle = prec, driver, timing, bundle  # delta: by precision
     hisq.hisq_set_solver_params(p)
 
 
@@ -474,7 +477,7 @@ def run_ours(args, rank, world, local_rank, dist):
               "recompute_gflops": sum(acc.recompute_flops(Vh, s.reliable_updates) for s in stats) / (ph[3] / 1e3) / 1e9
               if ph[3] > 0 else None,
               "clock": "%globaltimer read by block 0 after each grid barrier"}
-    key = f"cg_persistent_{args.inner}_{'x'.join(map(str, dims))}_n{nb}"
+    key = f"cg_persistent_{args.inner}_{'x'.join(map(str, dims))}_n{nb}_delta{DEFAULT_DELTA[args.inner]}"
     traffic = kernel_traffic(key)
     binding = "alu" if frac_alu >= frac_hbm else "hbm"
     roofline = {"bound": binding,
@@ -663,6 +666,59 @@ def run_dslash(args):
                       "us": sec * 1e6, "gflops": acc.DSLASH_FLOPS_PER_SITE * n * lat.half_volume / sec / 1e9,
                       "gbs": byts / sec / 1e9, "frac_hbm": byts / sec / 1e9 / hbm_peak,
                       "shape_arg": ",".join(str(v) for v in shape)}), flush=True)
+    hisq.hisq_finalize()
+
+
+def run_slabs(args):
+    """The Dslash decomposed into 2 and 4 t-slabs with depth-3 ghost planes (all slabs on this GPU)
+    against the undecomposed Dslash of the same canonical input, --inner storage, 1 and 16
+    right-hand sides: median CUDA-event times of face packing, interior kernels, halo copies and the
+    whole decomposed Dslash (scatter and gather excluded), L2 flushed before each launch."""
+    import torch
+    import hisq_inputs as hi
+    from paper_1409_1510_gb300 import hisq
+    dims, _ = workload(args)
+    lat = hi.Lattice(dims)
+    X, N = hi.fat_links(lat), hi.naik_links(lat)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    hisq.hisq_init(dims, 0, stream)
+    d64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.float64).copy()).to(dev)
+    prec = PREC[args.inner]
+    Xd, Nd = d64(X), d64(N)
+    fat = hisq.hisq_links_create(Xd, False, prec, 18)
+    naik = hisq.hisq_links_create(Nd, True, prec, 18)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    out = {"mode": "slabs", "lattice": list(dims), "precision": args.inner, "runs": []}
+    for n in (1, 16):
+        vin = d64(np.stack([hi.gaussian_rhs(lat, k) for k in range(n)]))
+        vout = torch.empty_like(vin)
+        packed = torch.empty(hisq.hisq_vector_bytes(prec, n), dtype=torch.uint8, device=dev)
+        hisq.hisq_pack(vin, packed, n, prec)
+        pout = torch.empty_like(packed)
+        hisq.hisq_autotune(fat, naik, n)
+        ts = []
+        for i in range(max(args.steps, 5)):
+            flush.zero_()
+            ts.append(event_ms(torch, stream, lambda: hisq.hisq_dslash(fat, naik, packed, pout, n, 0)))
+        whole_ms = statistics.median(ts)
+        for nslab in (2, 4):
+            h = hisq.hisq_slabs_create(Xd, Nd, prec, nslab)
+            ms = np.zeros(4)
+            hisq.hisq_slabs_dslash(h, vin, vout, n, 0, ms)  # warm-up
+            rows = []
+            for i in range(max(args.steps, 5)):
+                flush.zero_()
+                torch.cuda.synchronize()
+                hisq.hisq_slabs_dslash(h, vin, vout, n, 0, ms)
+                rows.append(ms.copy())
+            med = np.median(np.stack(rows), axis=0)
+            out["runs"].append({"nrhs": n, "slabs": nslab, "planes_per_slab": dims[3] // nslab,
+                                "face_pack_ms": med[0], "interior_ms": med[1], "halo_copy_ms": med[2],
+                                "decomposed_ms": med[3], "undecomposed_ms": whole_ms,
+                                "overhead": med[3] / whole_ms - 1.0})
+            hisq.hisq_slabs_destroy(h)
+    print(json.dumps(out), flush=True)
     hisq.hisq_finalize()
 
 
@@ -1131,6 +1187,9 @@ def main():
         return
     if args.mode == "production":
         run_production(args)
+        return
+    if args.mode == "slabs":
+        run_slabs(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

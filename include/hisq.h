@@ -218,7 +218,10 @@ int hisq_aop_noalloc(const hisq_links *fat, const hisq_links *naik, double mass,
 typedef struct {
     int inner_prec;       /* HISQ_FP64: plain FP64 CG; FP32/FP16/BF16: mixed precision with FP64
                              reliable updates (needs links packed in that precision) */
-    double delta;         /* reliable update when |r| < delta * |r at the last update| (0.1) */
+    double delta;         /* reliable update when |r| < delta * |r at the last update|; 0
+                             (default) = by inner precision: FP32 0.01, FP16 0.03, BF16 0.1 (the
+                             iterated residual follows the operator of the stored links, so a
+                             coarser storage needs updates at smaller drops); else in (0, 1) */
     int max_iter;         /* per right-hand side (default 20000) */
     int bundle;           /* right-hand sides per bundle, 1..HISQ_MAX_BUNDLE; 0 (default) = the
                              autotuner's choice among 1, 2, 4, 8, 12, 16 and min(nrhs, 16): the

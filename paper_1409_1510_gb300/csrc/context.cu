@@ -476,7 +476,7 @@ void hisq_default_solver_params(hisq_solver_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->inner_prec = HISQ_FP32;
-    p->delta = 0.1;
+    p->delta = 0.0;  // by inner precision (default_delta)
     p->max_iter = 20000;
     p->bundle = 0;
     p->use_graph = 2;

@@ -658,6 +658,22 @@ static int enqueue_setup(const Solve &S) {
     return blas(S, HOOK_INIT);
 }
 
+// The reliable-update threshold when the caller leaves it to the library.  Between updates the
+// iterated residual follows b - A' x with A' the operator of the links in the storage precision,
+// so it drifts from the true residual by about (A - A') x_lo, a multiple of the storage rounding;
+// an update threshold below that drift makes the iterated residual reach the tolerance while the
+// true one has not, and every such false convergence costs a recomputation.  Measured at 32^3 x 8
+// (m = 0.01) and 64^3 x 16 (m = 0.002): FP16 storage breaks down below 0.003, BF16 below 0.03, FP32
+// not down to 0.001; each default sits about ten times above its breakdown (at FP16 and 64^3 x 16,
+// 0.01 already costs more in added iterations than it saves in recomputations).
+static double default_delta(int prec) {
+    switch (prec) {
+    case HISQ_FP32: return 0.01;
+    case HISQ_FP16: return 0.03;
+    default: return 0.1;
+    }
+}
+
 static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned long long h_upd, double tol) {
     const hisq_solver_params &P = S.ctx->params;
     SolverState *h = S.w->h_st;
@@ -672,7 +688,7 @@ static int set_state_params(const Solve &S, unsigned long long h_loop, unsigned 
         h->tolk[k] = (S.tolv ? S.tolv[k] : tol) * TOL_SAFETY;
         h->mass2[k] = S.mass2v ? S.mass2v[k] : S.mass * S.mass;
     }
-    h->delta = P.delta;
+    h->delta = P.delta > 0.0 ? P.delta : default_delta(S.prec);
     h->h_loop = h_loop;
     h->h_upd = h_upd;
     h->cond_loop = 1;  // the defaults the graph assigns at launch
@@ -1123,7 +1139,8 @@ int hisq_set_solver_params(const hisq_solver_params *p) {
     if (!p) return set_error(HISQ_ERR_ARG, "null params");
     if (p->inner_prec < HISQ_FP64 || p->inner_prec > HISQ_BF16) return set_error(HISQ_ERR_ARG, "bad inner precision");
     if (p->max_iter < 1) return set_error(HISQ_ERR_ARG, "max_iter must be >= 1");
-    if (!(p->delta > 0.0 && p->delta < 1.0)) return set_error(HISQ_ERR_ARG, "delta must be in (0, 1)");
+    if (!(p->delta == 0.0 || (p->delta > 0.0 && p->delta < 1.0)))
+        return set_error(HISQ_ERR_ARG, "delta must be 0 (by precision) or in (0, 1)");
     if (p->bundle < 0 || p->bundle > HISQ_MAX_BUNDLE) return set_error(HISQ_ERR_ARG, "bundle must be in 0..%d", HISQ_MAX_BUNDLE);
     if (p->pc && p->pc->ctx != ctx) return set_error(HISQ_ERR_STATE, "preconditioner of another context");
     ctx->params = *p;

@@ -236,3 +236,27 @@ def test_l2_resident_links_do_not_change_the_solve():
             runs.append(int(iters[0]))
         assert max(runs) - min(runs) <= 1
         assert g.oracle.true_residual(b, x[0], 0.01)[0] <= TOL * SLACK
+
+
+def test_reliable_update_threshold_by_precision():
+    """delta = 0 (the default) takes the threshold of the inner precision (FP16: 0.03); an explicit
+    delta in (0, 1) overrides it; other values are rejected.  Every variant meets the oracle's true
+    residual, and the smaller FP16 default recomputes no more often than 0.1."""
+    dims = (8, 10, 8, 6)
+    mass = 0.05
+    with gpu(dims, 2) as g:
+        assert g.hisq.hisq_default_solver_params().delta == 0.0
+        p = g.hisq.hisq_default_solver_params()
+        for bad in (1.0, -0.1, 1.5):
+            p.delta = bad
+            with pytest.raises(g.hisq.HisqError):
+                g.hisq.hisq_set_solver_params(p)
+        rhs = [hi.gaussian_rhs(g.lat, k) for k in range(2)]
+        updates = {}
+        for delta in (0.0, 0.1):
+            x, stats, iters, res = _solve(g, rhs, mass, inner_prec=2, delta=delta)
+            true = g.oracle.true_residual(np.stack(rhs), x, mass)
+            assert np.all(true <= TOL * SLACK), (delta, true)
+            assert stats.converged == 2
+            updates[delta] = stats.reliable_updates
+        assert updates[0.0] <= updates[0.1], updates
