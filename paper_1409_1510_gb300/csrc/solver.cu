@@ -878,6 +878,12 @@ static int solve_bundle_persistent(Solve &S, double tol, bool *done) {
     LaunchShape sh = tuned_shape(S.ctx, S.fat, S.naik, S.n, S.prec == HISQ_FP64 ? LINKS_FP64 : LINKS_INNER);
     int R = sh.R > 4 ? 4 : sh.R;
     if (S.prec == HISQ_FP64 && R > 2) R = 2;  // four FP64 right-hand sides per thread would spill
+    // four FP32 right-hand sides per thread fit the separate Dslash kernel (up to 255 registers) but
+    // not the persistent kernel's 128: measured at 48^3 x 12, bundles of 4 and 16, two per thread
+    // run the persistent solve 1.6x and 1.3x faster than four (and faster than the graph driver);
+    // BF16 (its vectors unpacked by shifts, one register per value) 5% faster at 64^3 x 16 and 16
+    // right-hand sides.  FP16 keeps four (its records unpack into packed pairs): 3% faster there.
+    if ((S.prec == HISQ_FP32 || S.prec == HISQ_BF16) && R > 2) R = 2;
     while (S.n % R) R /= 2;
     // block size: the parameter if set (a multiple of 32 up to the kernel's bound), else 512
     int threads = std::min(pers_threads(R), PERS_DEFAULT_THREADS);
