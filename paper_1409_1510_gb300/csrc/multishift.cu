@@ -4,12 +4,17 @@
 // so an iteration costs one A p (the two multi-right-hand-side Dslash kernels with the fused
 // <p, A p>) plus, per shift, one fused pass over x_j and p_j.
 //
-// The shared iteration is one CUDA graph: setup, then a WHILE conditional node whose body is
+// The shared iteration runs after two setup kernels as one persistent cooperative kernel
+// (use_graph = 2, the default, with 18-real Naik links and a co-resident grid), whose phases are
+// separated by the bounded grid barrier of the persistent CG solve and whose blocks each evolve a
+// shared-memory copy of the state identically (the same summed partials, the same scalar step):
 //   t = D_oe p;  A p = m_base^2 p - D_eo t with <p, A p>;
 //   update: for every live shift  p_j = zeta_j r + beta_j p_j,  x_j += alpha_j p_j;
 //           r -= alpha A p with |r|^2;
-//   p = r + beta p, and (last block) the scalar step: new zeta_j, beta, per-shift convergence,
-//   the loop condition.
+//   p = r + beta p; the scalar step: new zeta_j, beta, per-shift convergence, the loop condition.
+// Otherwise the same iteration is one CUDA graph: setup, then a WHILE conditional node whose body
+// launches the two Dslash kernels and the update and direction kernels below (the last block of
+// the direction kernel runs the scalar step and sets the loop condition).
 // The per-shift direction update is deferred into the next iteration's update pass, so each
 // shift costs one read and one write of x_j and p_j per iteration.  The blocks of the update
 // and direction kernels derive alpha, beta and the zeta's from the same state and the same
@@ -29,6 +34,7 @@
 
 #include "hisq_internal.cuh"
 #include "dslash_kernel.cuh"
+#include "cg_persistent.cuh"
 
 namespace hisq {
 
@@ -274,6 +280,205 @@ __global__ void __launch_bounds__(MS_THREADS) ms_direction_kernel(MsArgs a) {
     set_condition(m.h_loop, &m.cond_last, (unsigned)m.any_live);
 }
 
+// ---- the shared iteration as one persistent cooperative kernel ----
+struct MsPersArgs {
+    PersArgs pa;   // geometry, links of the iteration, p, t, ap, n = 1, partials, barrier, error flag
+    MsArgs ms;     // r, x_j, p_j, the state (read at the start, written back by block 0 at the end)
+    double mass2;  // m^2 + sigma_base
+};
+
+constexpr int MS_PERS_THREADS = 512;
+
+// Per live shift j, from the state and this iteration's alpha: its list position, zeta_j, alpha_j
+// and beta_j (thread 0; the same coefficients as ms_update_kernel's)
+__device__ __forceinline__ int ms_coefficients(const MsState &m, int nshift, double al, int *list, double *zeta,
+                                               double *aj, double *bj) {
+    int nl = 0;
+    for (int j = 0; j < nshift; j++) {
+        if (!m.live[j]) continue;
+        const double zn = ms_zeta_next(m, j, al);
+        const double ratio = m.zeta[j] / m.zeta_old[j];
+        list[nl] = j;
+        zeta[nl] = m.zeta[j];
+        aj[nl] = al * zn / m.zeta[j];
+        bj[nl] = m.k == 0 ? 0.0 : m.beta_prev * ratio * ratio;
+        nl++;
+    }
+    return nl;
+}
+
+// The state's advance after |r_new|^2 (thread 0; ms_direction_kernel's last block does the same)
+__device__ __forceinline__ void ms_advance(MsState &m) {
+    if (!m.any_live) return;
+    double al;
+    const bool ok = ms_alpha(m, &al) && isfinite(m.rr_new);
+    if (!ok) {
+        m.breakdown = 1;
+        m.any_live = 0;
+        return;
+    }
+    const double rr_new = m.rr_new;
+    int live = 0;
+    for (int j = 0; j < m.nshift; j++) {
+        if (!m.live[j]) continue;
+        const double zn = ms_zeta_next(m, j, al);
+        m.zeta_old[j] = m.zeta[j];
+        m.zeta[j] = zn;
+        if (zn * zn * rr_new <= m.tol2) {
+            m.live[j] = 0;
+            m.stop_iter[j] = m.k + 1;
+        } else {
+            live++;
+        }
+    }
+    m.beta_prev = rr_new / m.rr;
+    m.alpha_prev = al;
+    m.rr = rr_new;
+    m.k++;
+    m.any_live = live > 0 && m.k < m.max_iter;
+}
+
+template <int P>
+__global__ void __launch_bounds__(MS_PERS_THREADS, P == HISQ_FP64 ? 1 : 2) ms_persistent_kernel(const __grid_constant__ MsPersArgs A) {
+    constexpr int Q = q_prec(P);
+    using rq = typename Prec<Q>::real;
+    using rp = typename Prec<P>::real;
+    extern __shared__ double red[];
+    __shared__ MsState m;
+    __shared__ double dots[4], m2v[1];
+    __shared__ int mask[1];
+    __shared__ double s_zeta[MS_MAX], s_aj[MS_MAX], s_bj[MS_MAX];
+    __shared__ int s_list[MS_MAX], s_nlive, s_ok;
+    __shared__ double s_alpha, s_beta;
+    const PersArgs &a = A.pa;
+    const int tid = threadIdx.x;
+    {
+        constexpr int WORDS = sizeof(MsState) / sizeof(uint32_t);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(A.ms.st);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&m);
+        for (int i = tid; i < WORDS; i += blockDim.x) dst[i] = __ldcg(src + i);
+        if (tid == 0) {
+            mask[0] = 1;
+            m2v[0] = A.mass2;
+        }
+    }
+    __syncthreads();
+    const VecView<Q> vr{A.ms.r, 1};
+    const VecView<P> vap{a.ap, 1}, vp{a.p, 1};
+    const size_t qb = A.ms.qbytes;
+    const long stride = (long)gridDim.x * blockDim.x;
+    bool ok = true;
+    while (m.any_live) {
+        dslash_phase<P, 1, EPI_PLAIN, Q>(a, a.fat, a.naik, PlainIn<P, true>{vp}, a.t, 1, mask, PlainIn<P, true>{vp},
+                                         nullptr, nullptr, red, m2v);
+        if (!(ok = grid_sync(a))) break;
+        dslash_phase<P, 1, EPI_AOP, Q>(a, a.fat, a.naik, PlainIn<P, true>{VecView<P>{a.t, 1}}, a.ap, 0, mask,
+                                       PlainIn<P, true>{vp}, nullptr, nullptr, red, m2v);
+        if (!(ok = grid_sync(a))) break;
+        sum_partials(a, red, 1, dots);
+        if (tid == 0) {
+            m.pap = dots[0];
+            double al;
+            s_ok = ms_alpha(m, &al) && m.any_live;
+            s_alpha = al;
+            s_nlive = ms_coefficients(m, A.ms.nshift, al, s_list, s_zeta, s_aj, s_bj);
+        }
+        __syncthreads();
+        // update pass: p_j, x_j for the live shifts; r -= alpha A p with |r|^2
+        double acc[1] = {0.0};
+        if (s_ok) {
+            const rq al = (rq)s_alpha;
+            const int nl = s_nlive;
+            for (long s = (long)blockIdx.x * blockDim.x + tid; s < a.g.Vh; s += stride) {
+                Cplx<rq> rv[3];
+                Cplx<rp> ap[3];
+                load_vec<Q, true>(vr, s, 0, rv);
+                load_vec<P, true>(vap, s, 0, ap);
+                for (int i = 0; i < nl; i++) {
+                    const int j = s_list[i];
+                    const VecView<Q> vx{(char *)A.ms.xs + (size_t)j * qb, 1}, vpj{(char *)A.ms.ps + (size_t)j * qb, 1};
+                    const rq z = (rq)s_zeta[i], bj = (rq)s_bj[i], aj = (rq)s_aj[i];
+                    Cplx<rq> pj[3], xj[3];
+                    if (s_bj[i] != 0.0) {
+                        load_vec<Q, true>(vpj, s, 0, pj);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; c++) pj[c] = {0, 0};
+                    }
+                    load_vec<Q, true>(vx, s, 0, xj);
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        pj[c] = {z * rv[c].re + bj * pj[c].re, z * rv[c].im + bj * pj[c].im};
+                        xj[c] = {xj[c].re + aj * pj[c].re, xj[c].im + aj * pj[c].im};
+                    }
+                    store_vec<Q>(vpj, s, 0, pj);
+                    store_vec<Q>(vx, s, 0, xj);
+                }
+                rq part = 0;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    rv[c] = {rv[c].re - al * (rq)ap[c].re, rv[c].im - al * (rq)ap[c].im};
+                    part += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+                }
+                acc[0] += (double)part;
+                store_vec<Q>(vr, s, 0, rv);
+            }
+        }
+        // |r|^2 goes to partials column 1: a block that is through its update may publish while a
+        // slower one still sums column 0 (<p, A p>) of this iteration
+        publish_dots<1>(a, red, acc, 1, 0, 1, 1);
+        if (!(ok = grid_sync(a))) break;
+        sum_partials(a, red, 2, dots);
+        if (tid == 0) {
+            m.rr_new = s_ok ? dots[1] : 0.0;
+            double al;
+            s_ok = ms_alpha(m, &al) && m.any_live && isfinite(m.rr_new);
+            s_beta = s_ok ? m.rr_new / m.rr : 0.0;
+        }
+        __syncthreads();
+        // direction: p = r + beta p, then the scalar step (every block the same)
+        if (s_ok) {
+            const rp be = (rp)s_beta;
+            for (long s = (long)blockIdx.x * blockDim.x + tid; s < a.g.Vh; s += stride) {
+                Cplx<rq> rv[3];
+                Cplx<rp> p[3];
+                load_vec<Q, true>(vr, s, 0, rv);
+                load_vec<P, true>(vp, s, 0, p);
+#pragma unroll
+                for (int c = 0; c < 3; c++) p[c] = {(rp)rv[c].re + be * p[c].re, (rp)rv[c].im + be * p[c].im};
+                store_vec<P>(vp, s, 0, p);
+            }
+        }
+        if (tid == 0) ms_advance(m);
+        if (!(ok = grid_sync(a))) break;  // p complete before the next D_oe; the state advanced everywhere
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        constexpr int WORDS = sizeof(MsState) / sizeof(uint32_t);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&m);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(A.ms.st);
+        for (int i = tid; i < WORDS; i += blockDim.x) dst[i] = src[i];
+    }
+    (void)ok;
+}
+
+template <int P>
+static cudaError_t ms_persistent_launch(const MsPersArgs &a, int grid, size_t smem, cudaStream_t st) {
+    void *args[] = {const_cast<MsPersArgs *>(&a)};
+    const void *k = (const void *)ms_persistent_kernel<P>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, grid, MS_PERS_THREADS, args, smem, st);
+}
+
+template <int P>
+static cudaError_t ms_persistent_occupancy(size_t smem, int *per_sm) {
+    const void *k = (const void *)ms_persistent_kernel<P>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, MS_PERS_THREADS, smem);
+}
+
 // x += y on canonical FP64 arrays of `count` doubles
 __global__ void __launch_bounds__(256) ms_axpy_canon_kernel(double *x, const double *y, long count) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
@@ -289,6 +494,8 @@ struct MsWork {
     double *partials = nullptr;
     size_t partials_cap = 0;
     unsigned int *counter = nullptr;
+    unsigned int *bar = nullptr;  // the persistent kernel's grid-barrier word
+    int *err = nullptr;           // set when one of its barrier waits ran out
     MsState *st = nullptr, *h_st = nullptr;
     // the captured shared iteration and what it was captured for
     cudaGraphExec_t exec = nullptr;
@@ -327,6 +534,8 @@ void free_multishift(hisq_ctx *ctx) {
     ms_free_buffers(w);
     if (w->partials) cudaFree(w->partials);
     if (w->counter) cudaFree(w->counter);
+    if (w->bar) cudaFree(w->bar);
+    if (w->err) cudaFree(w->err);
     if (w->st) cudaFree(w->st);
     if (w->h_st) cudaFreeHost(w->h_st);
     delete w;
@@ -340,6 +549,7 @@ static int ms_workspace(hisq_ctx *ctx, int nshift, int prec) {
         w->partials_cap = (size_t)ctx->num_sms * 64 * 4;
         if (cudaMalloc(&w->partials, w->partials_cap * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&w->counter, 4 * sizeof(unsigned int)) != cudaSuccess ||
+            cudaMalloc(&w->bar, 4 * sizeof(unsigned int)) != cudaSuccess || cudaMalloc(&w->err, 4 * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&w->st, sizeof(MsState)) != cudaSuccess || cudaMallocHost(&w->h_st, sizeof(MsState)) != cudaSuccess)
             return set_error(HISQ_ERR_NOMEM, "multi-shift workspace allocation failed");
         cudaMemset(w->counter, 0, 4 * sizeof(unsigned int));
@@ -519,6 +729,63 @@ static int ms_build(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_
     }
 }
 
+// The shared iteration as the persistent kernel: the two setup kernels, then one cooperative launch.
+// *done = false (nothing launched past the setup, which the graph repeats) when it does not apply:
+// 13- or 9-real Naik links, or a grid that cannot be co-resident.
+template <int P>
+static int ms_run_persistent(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, int nshift,
+                             double mass2_base, bool *done) {
+    *done = false;
+    if (naik->recon != 18) return HISQ_OK;
+    const size_t smem = (size_t)(4 * MS_PERS_THREADS + 64) * sizeof(double);
+    int per_sm = 0;
+    if (ms_persistent_occupancy<P>(smem, &per_sm) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return HISQ_OK;
+    }
+    const int grid = per_sm * ctx->num_sms;  // one resident wave
+    if ((size_t)grid * PERS_ND > w->partials_cap) return HISQ_OK;
+    MsPersArgs a;
+    memset(&a, 0, sizeof(a));
+    const bool links64 = P == HISQ_FP64 && fat->prec != HISQ_FP64;
+    a.pa.g = ctx->geom;
+    a.pa.fat = links64 ? fat->field64() : fat->field();
+    a.pa.naik = links64 ? naik->field64() : naik->field();
+    a.pa.p = w->p;
+    a.pa.t = w->t;
+    a.pa.ap = w->ap;
+    a.pa.n = 1;
+    a.pa.partials = w->partials;
+    a.pa.bar = w->bar;
+    a.pa.err = w->err;
+    a.pa.spin_limit = 1LL << 22;  // a barrier wait gives up after about a second
+    a.pa.expected = grid;
+    a.ms = ms_args(ctx, w, nshift);
+    a.mass2 = mass2_base;
+    cudaStream_t st = ctx->stream;
+    HISQ_CHECK(ms_enqueue_setup<P>(ctx, w, nshift, st));
+    HISQ_CUDA(cudaMemsetAsync(w->bar, 0, 4 * sizeof(unsigned int), st));
+    HISQ_CUDA(cudaMemsetAsync(w->err, 0, 4 * sizeof(int), st));
+    const cudaError_t e = ms_persistent_launch<P>(a, grid, smem, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+        cudaGetLastError();
+        return HISQ_OK;
+    }
+    if (e != cudaSuccess) return set_error(HISQ_ERR_CUDA, "multi-shift persistent launch failed: %s", cudaGetErrorString(e));
+    *done = true;
+    return HISQ_OK;
+}
+
+static int ms_persistent(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, int nshift, int prec,
+                         double mass2_base, bool *done) {
+    switch (prec) {
+    case HISQ_FP64: return ms_run_persistent<HISQ_FP64>(ctx, w, fat, naik, nshift, mass2_base, done);
+    case HISQ_FP32: return ms_run_persistent<HISQ_FP32>(ctx, w, fat, naik, nshift, mass2_base, done);
+    case HISQ_FP16: return ms_run_persistent<HISQ_FP16>(ctx, w, fat, naik, nshift, mass2_base, done);
+    default: return ms_run_persistent<HISQ_BF16>(ctx, w, fat, naik, nshift, mass2_base, done);
+    }
+}
+
 // |b - (m^2 + sigma) x - (-D_eo D_oe x)|^2 in FP64 for the canonical x; the residual stays in r64
 static int ms_residual(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, const double *x_canon,
                        double mass2, double *res2) {
@@ -599,9 +866,6 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     // ---- the shared iteration ----
     HISQ_CUDA(cudaMemcpyAsync(w->canon_b, rhs, vbytes, cudaMemcpyDefault, st));
     HISQ_CHECK(pack_vectors(ctx, w->canon_b, w->b64, 1, HISQ_FP64, st));
-    const bool reuse = w->exec && w->fat == fat && w->naik == naik && w->mass2_base == mass2_base &&
-                       w->g_nshift == nshift && w->g_prec == prec && w->tune_generation == ctx->tune_generation;
-    if (!reuse) HISQ_CHECK(ms_build(ctx, w, fat, naik, nshift, prec, mass2_base));
     MsState *h = w->h_st;
     memset(h, 0, sizeof(MsState));
     h->nshift = nshift;
@@ -611,22 +875,36 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     h->tol = tol_shared;
     h->alpha_prev = 1.0;
     h->beta_prev = 0.0;
-    h->h_loop = w->h_loop;
+    h->h_loop = 0;
     for (int j = 0; j < nshift; j++) {
         h->live[j] = 1;
         h->stop_iter[j] = -1;
         h->s[j] = shifts[j] - sigma_base;
         h->zeta[j] = h->zeta_old[j] = 1.0;
     }
-    if (!w->h_loop) return set_error(HISQ_ERR_STATE, "multi-shift graph without its loop handle");
-    HISQ_CUDA(cudaMemcpyAsync(w->st, h, sizeof(MsState), cudaMemcpyHostToDevice, st));
-    HISQ_CUDA(cudaGraphLaunch(w->exec, st));
+    bool persistent = false;
+    if (P0.use_graph == 2) {
+        HISQ_CUDA(cudaMemcpyAsync(w->st, h, sizeof(MsState), cudaMemcpyHostToDevice, st));
+        HISQ_CHECK(ms_persistent(ctx, w, fat, naik, nshift, prec, mass2_base, &persistent));
+    }
+    if (!persistent) {
+        const bool reuse = w->exec && w->fat == fat && w->naik == naik && w->mass2_base == mass2_base &&
+                           w->g_nshift == nshift && w->g_prec == prec && w->tune_generation == ctx->tune_generation;
+        if (!reuse) HISQ_CHECK(ms_build(ctx, w, fat, naik, nshift, prec, mass2_base));
+        if (!w->h_loop) return set_error(HISQ_ERR_STATE, "multi-shift graph without its loop handle");
+        h->h_loop = w->h_loop;
+        HISQ_CUDA(cudaMemcpyAsync(w->st, h, sizeof(MsState), cudaMemcpyHostToDevice, st));
+        HISQ_CUDA(cudaGraphLaunch(w->exec, st));
+    }
     const int Q = q_prec(prec);
     const size_t qbytes = vector_bytes(Q, Vh, 1);
     for (int j = 0; j < nshift; j++)
         HISQ_CHECK(unpack_vectors(ctx, (const char *)w->xs + (size_t)j * qbytes, w->canon_x + (size_t)j * Vh * 6, 1, Q, st));
     HISQ_CUDA(cudaMemcpyAsync(h, w->st, sizeof(MsState), cudaMemcpyDeviceToHost, st));
+    int err_h = 0;
+    if (persistent) HISQ_CUDA(cudaMemcpyAsync(&err_h, w->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     HISQ_CUDA(cudaStreamSynchronize(st));
+    if (err_h) return set_error(HISQ_ERR_TIMEOUT, "a grid barrier of the persistent multi-shift iteration ran out of its wait budget");
     const double t_shared = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     const MsState shared = *h;
     if (shared.breakdown) return set_error(HISQ_ERR_BREAKDOWN, "multi-shift CG breakdown (non-positive <p, A p> or NaN)");

@@ -35,12 +35,14 @@ def _true(g, b, xs, shifts, mass):
     return np.array([g.oracle.true_residual(b, xs[j], math.sqrt(mass * mass + s))[0] for j, s in enumerate(shifts)])
 
 
-def test_fp64_multishift_matches_oracle():
-    """FP64 throughout: every shift meets the true residual, agrees with the oracle's multi-shift
-    solution, and stops at the oracle's iteration (within two)."""
+@pytest.mark.parametrize("driver", [2, 1])
+def test_fp64_multishift_matches_oracle(driver):
+    """FP64 throughout, shared iteration as the persistent kernel (2) or the captured graph (1):
+    every shift meets the true residual, agrees with the oracle's multi-shift solution, and stops
+    at the oracle's iteration (within two)."""
     with gpu(DIMS, 0) as g:
         b = hi.gaussian_rhs(g.lat, 21)
-        xs, stats, iters, res = _ms(g, b, SHIFTS, MASS, inner_prec=0)
+        xs, stats, iters, res = _ms(g, b, SHIFTS, MASS, inner_prec=0, use_graph=driver)
         assert np.all(_true(g, b, xs, SHIFTS, MASS) <= TOL * SLACK)
         assert np.all(res <= TOL) and stats.converged == len(SHIFTS)
         xo, it, its, rels = g.oracle.cg_multishift(b, SHIFTS, MASS, TOL)
@@ -51,13 +53,14 @@ def test_fp64_multishift_matches_oracle():
         assert abs(stats.shared_iterations - it) <= 2
 
 
+@pytest.mark.parametrize("driver", [2, 1])
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_mixed_precision_every_shift_reaches_fp64_residual(prec):
+def test_mixed_precision_every_shift_reaches_fp64_residual(prec, driver):
     """Low-precision shared iteration plus FP64 defect correction per shift: every shift reaches
     the oracle's true residual 1e-10."""
     with gpu(DIMS, prec) as g:
         b = hi.gaussian_rhs(g.lat, 22)
-        xs, stats, iters, res = _ms(g, b, SHIFTS, MASS, inner_prec=prec)
+        xs, stats, iters, res = _ms(g, b, SHIFTS, MASS, inner_prec=prec, use_graph=driver)
         true = _true(g, b, xs, SHIFTS, MASS)
         assert np.all(true <= TOL * SLACK), true
         assert stats.converged == len(SHIFTS) and np.all(res <= TOL)
@@ -104,3 +107,21 @@ def test_invalid_arguments_are_rejected():
         assert h.hisq_cg_multishift(g.fat, g.naik, b, many, [0.0] * len(many), MASS, TOL, raise_on_error=False) == -1
         assert h.hisq_cg_multishift(g.fat, g.naik, b, [np.zeros_like(b)], [0.0], MASS, -1.0,
                                     raise_on_error=False) == -1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_persistent_and_graph_shared_iterations_agree(prec):
+    """The two drivers of the shared iteration run the same recurrences: the same number of
+    shared iterations (within one: their block sums add in different orders) and, in FP64,
+    solutions that agree as closely as the oracle's does with either (1e-7)."""
+    with gpu(DIMS, prec) as g:
+        b = hi.gaussian_rhs(g.lat, 24)
+        out = {}
+        for driver in (2, 1):
+            xs, stats, iters, res = _ms(g, b, SHIFTS, MASS, inner_prec=prec, use_graph=driver)
+            out[driver] = (xs, stats.shared_iterations)
+        assert abs(out[2][1] - out[1][1]) <= 1, (out[2][1], out[1][1])
+        if prec == 0:
+            for j in range(len(SHIFTS)):
+                d = np.linalg.norm(out[2][0][j] - out[1][0][j]) / np.linalg.norm(out[1][0][j])
+                assert d <= 1e-7, (j, d)
