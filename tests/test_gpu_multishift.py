@@ -78,9 +78,9 @@ def test_single_zero_shift_is_plain_cg():
 
 
 def test_zero_rhs_and_repeated_calls():
-    """b = 0 gives x_j = 0 without iterating; two identical calls (the captured graph reused with
-    its state reset) give identical solutions; a call with other shifts of the same smallest
-    shift reuses the graph and still meets the residual."""
+    """b = 0 gives x_j = 0 without iterating; two identical calls (the state reset at every call)
+    give identical solutions; a call with other shifts of the same smallest shift still meets the
+    residual."""
     with gpu(DIMS, 1) as g:
         zero = np.zeros((g.lat.half_volume, 3), dtype=np.complex128)
         xs, stats, _, res = _ms(g, zero, SHIFTS, MASS, inner_prec=1)
