@@ -386,8 +386,10 @@ int launch_dslash(hisq_ctx *ctx, const hisq_links *fat, const hisq_links *naik, 
     a.spb = spb;
     a.parity = d.parity;
     a.mass2 = d.mass2;
+    a.mass2v = d.mass2v;
     a.axpy = d.axpy_in;
     a.b = d.b;
+    a.b_one = d.b_one;
     a.out_lo = d.out_lo;
     a.lo_prec = d.lo_prec;
     a.active = d.active;

@@ -66,12 +66,14 @@ __global__ void __launch_bounds__(256) dslash_ds_kernel(KArgs a) {
                 if (!act[r]) continue;
                 double d = 0.0;
                 double2 w[3];
+                const double m2 = a.mass2v ? a.mass2v[r0 + r] : a.mass2;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     const long idx = ((long)s * 3 + c) * a.n + r0 + r;
-                    const double2 x = __ldg(vx + idx), b = __ldg(vb + idx);
-                    w[c].x = b.x - a.mass2 * x.x + ds_value(acc[r][c].re);
-                    w[c].y = b.y - a.mass2 * x.y + ds_value(acc[r][c].im);
+                    const long bidx = a.b_one ? (long)s * 3 + c : idx;
+                    const double2 x = __ldg(vx + idx), b = __ldg(vb + bidx);
+                    w[c].x = b.x - m2 * x.x + ds_value(acc[r][c].re);
+                    w[c].y = b.y - m2 * x.y + ds_value(acc[r][c].im);
                     d += w[c].x * w[c].x + w[c].y * w[c].y;
                 }
                 dot[r] += d;

@@ -35,8 +35,10 @@ struct KArgs {
     void *out;
     int n, t, spb, parity;
     double mass2;
+    const double *mass2v;  // EPI_RESID: m^2 per right-hand side (null: mass2)
     const void *axpy;
     const void *b;
+    int b_one;             // EPI_RESID: b is one right-hand side shared by the bundle
     void *out_lo;
     int lo_prec;
     const int *active;
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
         } else {
             static_assert(EPI == EPI_RESID && P == HISQ_FP64, "residual epilogue is FP64 only");
             const VecView<HISQ_FP64> vx = view<HISQ_FP64>(a.axpy, g.Vh, a.n);
-            const VecView<HISQ_FP64> vb = view<HISQ_FP64>(a.b, g.Vh, a.n);
+            const VecView<HISQ_FP64> vb = view<HISQ_FP64>(a.b, g.Vh, a.b_one ? 1 : a.n);
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 if (!act[r]) continue;
@@ -525,10 +527,11 @@ __global__ void __launch_bounds__(256) dslash_kernel(KArgs a) {
                 double d = 0.0;
                 Cplx<double> x[3], b[3];
                 load_vec<HISQ_FP64>(vx, s, r0 + r, x);
-                load_vec<HISQ_FP64>(vb, s, r0 + r, b);
+                load_vec<HISQ_FP64>(vb, s, a.b_one ? 0 : r0 + r, b);
+                const double m2 = a.mass2v ? a.mass2v[r0 + r] : a.mass2;
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    w[c] = {b[c].re - a.mass2 * x[c].re + (double)acc[r][c].re, b[c].im - a.mass2 * x[c].im + (double)acc[r][c].im};
+                    w[c] = {b[c].re - m2 * x[c].re + (double)acc[r][c].re, b[c].im - m2 * x[c].im + (double)acc[r][c].im};
                     d += w[c].re * w[c].re + w[c].im * w[c].im;
                 }
                 dot[r] += d;

@@ -393,8 +393,10 @@ struct DslashArgs {
     int parity;            // output parity
     Epilogue epi;
     double mass2;          // EPI_AOP / EPI_RESID
+    const double *mass2v;  // EPI_RESID: device m^2 per right-hand side (null: mass2 for all)
     const void *axpy_in;   // EPI_AOP: p (same precision); EPI_RESID: x_hi (FP64)
     const void *b;         // EPI_RESID: right-hand side b (FP64 internal)
+    int b_one;             // EPI_RESID: b holds one right-hand side, shared by all of the bundle
     void *out_lo;          // EPI_RESID: sloppy copy of the new residual (lo_prec) or null
     int lo_prec;
     const int *active;     // per-rhs mask (null = all)

@@ -49,7 +49,7 @@ struct MsState {
     double rr, rr_new, pap, bb;          // |r|^2, |r_new|^2, <p, A p>, |b|^2
     double tol, tol2;                    // relative tolerance of the shared iteration, (tol |b|)^2
     double alpha_prev, beta_prev;
-    double res2;                         // FP64 residual |b - (A + sigma) x|^2 of a refinement check
+    double m2[MS_MAX], res2v[MS_MAX];    // a batched refinement check: m^2 + sigma_j and |r_j|^2 per listed shift
     unsigned long long h_loop;           // the WHILE node's conditional handle
 };
 
@@ -546,7 +546,7 @@ static int ms_workspace(hisq_ctx *ctx, int nshift, int prec) {
     if (!ctx->ms) {
         MsWork *w = new MsWork();
         ctx->ms = w;
-        w->partials_cap = (size_t)ctx->num_sms * 64 * 4;
+        w->partials_cap = (size_t)ctx->num_sms * 64 * MS_MAX;  // a batched residual of every shift
         if (cudaMalloc(&w->partials, w->partials_cap * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&w->counter, 4 * sizeof(unsigned int)) != cudaSuccess ||
             cudaMalloc(&w->bar, 4 * sizeof(unsigned int)) != cudaSuccess || cudaMalloc(&w->err, 4 * sizeof(int)) != cudaSuccess ||
@@ -564,9 +564,9 @@ static int ms_workspace(hisq_ctx *ctx, int nshift, int prec) {
         {&w->b64, vector_bytes(HISQ_FP64, Vh, 1)}, {&w->r, vector_bytes(Q, Vh, 1)},
         {&w->p, vector_bytes(prec, Vh, 1)},        {&w->t, vector_bytes(prec, Vh, 1)},
         {&w->ap, vector_bytes(prec, Vh, 1)},       {&w->xs, vector_bytes(Q, Vh, 1) * cap},
-        {&w->ps, vector_bytes(Q, Vh, 1) * cap},    {&w->x64, vector_bytes(HISQ_FP64, Vh, 1)},
-        {&w->t64, vector_bytes(HISQ_FP64, Vh, 1)}, {&w->r64, vector_bytes(HISQ_FP64, Vh, 1)},
-        {&w->x_ds, vector_bytes(HISQ_DS, Vh, 1)},
+        {&w->ps, vector_bytes(Q, Vh, 1) * cap},    {&w->x64, vector_bytes(HISQ_FP64, Vh, cap)},
+        {&w->t64, vector_bytes(HISQ_FP64, Vh, cap)}, {&w->r64, vector_bytes(HISQ_FP64, Vh, cap)},
+        {&w->x_ds, vector_bytes(HISQ_DS, Vh, cap)},
         {(void **)&w->canon_b, canon},             {(void **)&w->canon_r, canon * cap},
         {(void **)&w->canon_e, canon * cap},       {(void **)&w->canon_x, canon * cap},
     };
@@ -786,17 +786,28 @@ static int ms_persistent(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const 
     }
 }
 
-// |b - (m^2 + sigma) x - (-D_eo D_oe x)|^2 in FP64 for the canonical x; the residual stays in r64
-static int ms_residual(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, const double *x_canon,
-                       double mass2, double *res2) {
+// The FP64 residuals r_q = b - (m^2 + sigma_{j_q} - D_eo D_oe) x_{j_q} of m listed shifts in one
+// bundle: the listed canonical x_j are gathered (device copies) and packed as an m-RHS FP64
+// bundle, the residual Dslash runs once over it with a mass per right-hand side and the single b
+// shared by all; the residuals are unpacked to canon_r[0..m) in list order and |r_q|^2 returned.
+static int ms_residuals(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hisq_links *naik, const int *js, int m,
+                        const double *m2, double *res2) {
     cudaStream_t st = ctx->stream;
-    // FP64 accuracy: double-single arithmetic on the ds link copy for low-precision links
+    const int Vh = ctx->geom.Vh;
+    const size_t vbytes = (size_t)Vh * 6 * sizeof(double);
     const int hp = links_hp(fat);
-    HISQ_CHECK(pack_vectors(ctx, x_canon, w->x64, 1, HISQ_FP64, st));
-    if (hp == LINKS_DS) HISQ_CHECK(split_vectors(ctx, w->x64, w->x_ds, 1, st));
+    // canon_e is free here (the corrections of the previous round were added already)
+    for (int q = 0; q < m; q++)
+        HISQ_CUDA(cudaMemcpyAsync(w->canon_e + (size_t)q * Vh * 6, w->canon_x + (size_t)js[q] * Vh * 6, vbytes,
+                                  cudaMemcpyDeviceToDevice, st));
+    HISQ_CHECK(pack_vectors(ctx, w->canon_e, w->x64, m, HISQ_FP64, st));
+    if (hp == LINKS_DS) HISQ_CHECK(split_vectors(ctx, w->x64, w->x_ds, m, st));
+    double m2h[MS_MAX];
+    for (int q = 0; q < m; q++) m2h[q] = m2[q];
+    HISQ_CUDA(cudaMemcpyAsync(w->st->m2, m2h, sizeof(double) * m, cudaMemcpyHostToDevice, st));
     DslashArgs d;
     memset(&d, 0, sizeof(d));
-    d.n = 1;
+    d.n = m;
     d.in = hp == LINKS_DS ? w->x_ds : w->x64;
     d.out = w->t64;
     d.parity = 1;
@@ -806,16 +817,18 @@ static int ms_residual(hisq_ctx *ctx, MsWork *w, const hisq_links *fat, const hi
     d.out = w->r64;
     d.parity = 0;
     d.epi = EPI_RESID;
-    d.mass2 = mass2;
+    d.mass2v = w->st->m2;
     d.axpy_in = w->x64;
     d.b = w->b64;
+    d.b_one = 1;
     d.partials = w->partials;
     d.partials_cap = w->partials_cap;
     d.counter = w->counter;
-    d.dot_out = &w->st->res2;
+    d.dot_out = w->st->res2v;
     d.hook = HOOK_NONE;
     HISQ_CHECK(launch_dslash(ctx, fat, naik, hp, d, nullptr, st));
-    HISQ_CUDA(cudaMemcpyAsync(res2, &w->st->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HISQ_CHECK(unpack_vectors(ctx, w->r64, w->canon_r, m, HISQ_FP64, st));
+    HISQ_CUDA(cudaMemcpyAsync(res2, w->st->res2v, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     HISQ_CUDA(cudaStreamSynchronize(st));
     return HISQ_OK;
 }
@@ -931,16 +944,24 @@ extern "C" int hisq_cg_multishift(const hisq_links *fat, const hisq_links *naik,
     }
     const double tol_acc = tol * TOL_SAFETY;  // acceptance bound of the library's FP64 residual
     for (int round = 0; round < 3 && bb > 0.0; round++) {
+        // the FP64 residuals of every shift not yet accepted, in one bundle
+        int chk[HISQ_MAX_SHIFTS], nchk = 0;
+        double chk_m2[HISQ_MAX_SHIFTS], chk_res2[HISQ_MAX_SHIFTS];
+        for (int j = 0; j < nshift; j++)
+            if (!(resid[j] <= tol_acc)) {
+                chk[nchk] = j;
+                chk_m2[nchk] = mass * mass + shifts[j];
+                nchk++;
+            }
+        if (nchk == 0) break;
+        HISQ_CHECK(ms_residuals(ctx, w, fat, naik, chk, nchk, chk_m2, chk_res2));
         int m = 0;
-        for (int j = 0; j < nshift; j++) {
+        for (int q = 0; q < nchk; q++) {
+            const int j = chk[q];
+            resid[j] = sqrt(chk_res2[q] / bb);
             if (resid[j] <= tol_acc) continue;
-            double res2 = 0.0;
-            HISQ_CHECK(ms_residual(ctx, w, fat, naik, w->canon_x + (size_t)j * Vh * 6, mass * mass + shifts[j], &res2));
-            resid[j] = sqrt(res2 / bb);
-            if (resid[j] <= tol_acc) continue;
-            HISQ_CHECK(unpack_vectors(ctx, w->r64, w->canon_r + (size_t)j * Vh * 6, 1, HISQ_FP64, st));
             idx[m] = j;
-            rp[m] = w->canon_r + (size_t)j * Vh * 6;
+            rp[m] = w->canon_r + (size_t)q * Vh * 6;  // ms_residuals left r_j at position q
             ep[m] = w->canon_e + (size_t)j * Vh * 6;
             m2v[m] = mass * mass + shifts[j];
             tolv[m] = 0.5 * tol / resid[j];
